@@ -1,0 +1,222 @@
+"""FP64 CPU oracle for CDR finite-element assembly (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library path never calls it.
+
+The arithmetic lives in ``fea_oracle.c`` (plain C, double precision, compiled
+with ``-ffp-contract=off`` so x86 and Arm give the same bits); this module only
+marshals numpy arrays.  ``build()`` compiles it with gcc into ``oracle/_build``.
+"""
+from __future__ import annotations
+
+import contextlib
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+TET4, HEX8, HEX27 = 0, 1, 2
+MASS, CONV, DIFF, REAC, SUPG = 1, 2, 4, 8, 16
+ALL_TERMS = 31
+OK, ERR_ARG, ERR_RANGE, ERR_DUP, ERR_INVERTED, ERR_CAP = 0, 1, 2, 3, 4, 5
+NEN = {TET4: 4, HEX8: 8, HEX27: 27}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fea_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libfea_oracle.so")
+_lib = None
+_lock = threading.Lock()
+
+_d = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i32 = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64 = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_L = C.c_int64
+_I = C.c_int
+_D = C.c_double
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2, no FP contraction)."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            L.or_set_mutation.argtypes = [_I]
+            L.or_shape.argtypes = [_I, _d, _d, _d]
+            L.or_quadrature.argtypes = [_I, _d, _d]
+            L.or_element.argtypes = [_I, _d, _d, _d, _d, _d, _D, _I, _d, _d]
+            L.or_validate.argtypes = [_I, _d, _L, _i32, _L]
+            L.or_incidence.argtypes = [_I, _i32, _L, _L, _i64, _i64]
+            L.or_pattern_rowptr.argtypes = [_I, _i32, _L, _L, _i64, _i64, _i64]
+            L.or_pattern_rowptr.restype = C.c_int64
+            L.or_pattern_colind.argtypes = [_I, _i32, _L, _i64, _i64, _i64, _i32]
+            L.or_posmap.argtypes = [_I, _i32, _L, _i64, _i32, _i32]
+            L.or_assemble.argtypes = [_I, _d, _L, _i32, _L, _L, _i64, _i32, _L, _d, _d, _d, _d, _D, _I, _I,
+                                      _d, _d, C.c_void_p, C.c_void_p]
+            L.or_row.argtypes = [_I, _d, _L, _i32, _i64, _i64, _L, _d, _d, _d, _d, _D, _I, _I, _L, _i32, _d, _d,
+                                 _d, _d]
+            L.or_row.restype = C.c_int64
+            L.or_apply.argtypes = [_I, _d, _L, _i32, _L, _d, _d, _d, _d, _D, _I, _I, _d, _d]
+            _lib = L
+    return _lib
+
+
+def _f(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _c(conn) -> np.ndarray:
+    return np.ascontiguousarray(conn, dtype=np.int32)
+
+
+@contextlib.contextmanager
+def mutation(m: int):
+    """Temporarily plant deliberate mistake ``m`` in the oracle (tests of the pins)."""
+    L = lib()
+    L.or_set_mutation(int(m))
+    try:
+        yield
+    finally:
+        L.or_set_mutation(0)
+
+
+def quadrature(elem_type: int):
+    xi = np.zeros(27 * 3)
+    w = np.zeros(27)
+    ng = lib().or_quadrature(elem_type, xi, w)
+    return xi[: 3 * ng].reshape(ng, 3).copy(), w[:ng].copy()
+
+
+def shape(elem_type: int, xi):
+    N = np.zeros(27)
+    dN = np.zeros(27 * 3)
+    nen = lib().or_shape(elem_type, _f(xi), N, dN)
+    return N[:nen].copy(), dN[: 3 * nen].reshape(nen, 3).copy()
+
+
+def element(elem_type, xe, ue, ke, se, phie, dt, terms=ALL_TERMS):
+    nen = NEN[elem_type]
+    Ae = np.zeros(nen * nen)
+    be = np.zeros(nen)
+    st = lib().or_element(elem_type, _f(xe).ravel(), _f(ue).ravel(), _f(ke), _f(se), _f(phie), float(dt),
+                          int(terms), Ae, be)
+    if st:
+        raise ValueError(f"oracle element error {st}")
+    return Ae.reshape(nen, nen), be
+
+
+def validate(elem_type, coords, conn) -> int:
+    conn = _c(conn)
+    return int(lib().or_validate(elem_type, _f(coords).ravel(), coords.shape[0], conn.ravel(), conn.shape[0]))
+
+
+def incidence(elem_type, conn, n_node):
+    conn = _c(conn)
+    inc_ptr = np.zeros(n_node + 1, dtype=np.int64)
+    inc_elem = np.zeros(conn.size, dtype=np.int64)
+    st = lib().or_incidence(elem_type, conn.ravel(), conn.shape[0], n_node, inc_ptr, inc_elem)
+    if st:
+        raise ValueError(f"oracle incidence error {st}")
+    return inc_ptr, inc_elem
+
+
+def pattern(elem_type, conn, n_node, with_pos=True):
+    """CSR pattern: rowptr (int64[N+1]), colind (int32[nnz]) and pos (int32[E,nen,nen])."""
+    conn = _c(conn)
+    inc_ptr, inc_elem = incidence(elem_type, conn, n_node)
+    rowptr = np.zeros(n_node + 1, dtype=np.int64)
+    nnz = lib().or_pattern_rowptr(elem_type, conn.ravel(), conn.shape[0], n_node, inc_ptr, inc_elem, rowptr)
+    if nnz < 0:
+        raise ValueError("oracle pattern error")
+    colind = np.zeros(nnz, dtype=np.int32)
+    st = lib().or_pattern_colind(elem_type, conn.ravel(), n_node, inc_ptr, inc_elem, rowptr, colind)
+    if st:
+        raise ValueError(f"oracle colind error {st}")
+    pos = None
+    if with_pos:
+        nen = NEN[elem_type]
+        pos = np.zeros((conn.shape[0], nen, nen), dtype=np.int32)
+        st = lib().or_posmap(elem_type, conn.ravel(), conn.shape[0], rowptr, colind, pos.ravel())
+        if st:
+            raise ValueError(f"oracle posmap error {st}")
+    return rowptr, colind, pos
+
+
+def assemble(elem_type, coords, conn, rowptr, colind, fields, terms=ALL_TERMS, e_range=None, with_abs=False):
+    """values (n_eq, nnz), rhs (n_eq, N) and, if asked, abs-sum denominators."""
+    conn = _c(conn)
+    n_node = coords.shape[0]
+    nnz = colind.shape[0]
+    n_eq = fields.diffusivity.shape[0]
+    values = np.zeros((n_eq, nnz))
+    rhs = np.zeros((n_eq, n_node))
+    absA = np.zeros((n_eq, nnz)) if with_abs else None
+    absb = np.zeros((n_eq, n_node)) if with_abs else None
+    e0, e1 = (0, conn.shape[0]) if e_range is None else e_range
+    st = lib().or_assemble(elem_type, _f(coords).ravel(), n_node, conn.ravel(), e0, e1,
+                           np.ascontiguousarray(rowptr, dtype=np.int64), _c(colind), nnz,
+                           _f(fields.velocity).ravel(), _f(fields.diffusivity).ravel(),
+                           _f(fields.reaction).ravel(), _f(fields.phi_old).ravel(), float(fields.dt), n_eq,
+                           int(terms), values.ravel(), rhs.ravel(),
+                           absA.ctypes.data if with_abs else None, absb.ctypes.data if with_abs else None)
+    if st:
+        raise ValueError(f"oracle assemble error {st}")
+    if with_abs:
+        return values, rhs, absA, absb
+    return values, rhs
+
+
+class RowSampler:
+    """Computes single rows of every equation from the elements incident to them."""
+
+    def __init__(self, elem_type, coords, conn, fields, terms=ALL_TERMS):
+        self.t = elem_type
+        self.coords = _f(coords).ravel()
+        self.n_node = coords.shape[0]
+        self.conn = _c(conn).ravel()
+        self.inc_ptr, self.inc_elem = incidence(elem_type, _c(conn), self.n_node)
+        self.f = (_f(fields.velocity).ravel(), _f(fields.diffusivity).ravel(), _f(fields.reaction).ravel(),
+                  _f(fields.phi_old).ravel())
+        self.dt = float(fields.dt)
+        self.n_eq = fields.diffusivity.shape[0]
+        self.terms = int(terms)
+        self.cap = int(np.max(np.diff(self.inc_ptr))) * NEN[elem_type] + 1
+
+    def row(self, r):
+        cap, q = self.cap, self.n_eq
+        cols = np.zeros(cap, dtype=np.int32)
+        vals = np.zeros(q * cap)
+        absv = np.zeros(q * cap)
+        rhs = np.zeros(q)
+        absr = np.zeros(q)
+        nc = lib().or_row(self.t, self.coords, self.n_node, self.conn, self.inc_ptr, self.inc_elem, int(r),
+                          *self.f, self.dt, q, self.terms, cap, cols, vals, absv, rhs, absr)
+        if nc < 0:
+            raise ValueError(f"oracle row error {-nc}")
+        vals = vals.reshape(q, cap)[:, :nc].copy()
+        absv = absv.reshape(q, cap)[:, :nc].copy()
+        return cols[:nc].copy(), vals, absv, rhs, absr
+
+
+def apply(elem_type, coords, conn, fields, q, x, terms=ALL_TERMS):
+    conn = _c(conn)
+    y = np.zeros(coords.shape[0])
+    st = lib().or_apply(elem_type, _f(coords).ravel(), coords.shape[0], conn.ravel(), conn.shape[0],
+                        _f(fields.velocity).ravel(), _f(fields.diffusivity).ravel(), _f(fields.reaction).ravel(),
+                        _f(fields.phi_old).ravel(), float(fields.dt), int(q), int(terms), _f(x), y)
+    if st:
+        raise ValueError(f"oracle apply error {st}")
+    return y

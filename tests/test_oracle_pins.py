@@ -1,0 +1,539 @@
+"""Pins of the FP64 oracle against what the mathematics fixes (CPU only).
+
+Each check reaches its expected value by a route that does not go through the
+oracle's own formulas: exact polynomial integration, closed forms of linear and
+box elements, conservation and consistency invariants, the patch test against
+face integrals of the boundary flux, brute-force dense assembly, and closed-form
+pattern counts.  ``test_pins_catch_planted_mistakes`` plants plausible errors in
+the oracle and checks that every one of them fails at least one pin.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from numpy.polynomial import polynomial as P
+
+import oracle as O
+from paper_2107_11541_gb300 import meshgen as G
+
+TYPES = (O.TET4, O.HEX8, O.HEX27)
+REF_VOLUME = {O.TET4: 1.0 / 6.0, O.HEX8: 8.0, O.HEX27: 8.0}
+
+
+def ref_nodes(t):
+    """Reference coordinates of the nodes in the documented local order."""
+    if t == O.TET4:
+        return np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    q = 2 if t == O.HEX8 else 3
+    pts = np.linspace(-1, 1, q)
+    return np.array([[pts[i], pts[j], pts[k]] for k in range(q) for j in range(q) for i in range(q)])
+
+
+# ------------------------------------------------------------------ reference element pins
+
+def check_quadrature(t):
+    xi, w = O.quadrature(t)
+    assert np.isclose(w.sum(), REF_VOLUME[t], rtol=0, atol=1e-14)
+    if t == O.TET4:  # exact for total degree <= 2: int x^a y^b z^c = a! b! c! / (a+b+c+3)!
+        for a in range(3):
+            for b in range(3 - a):
+                for c in range(3 - a - b):
+                    exact = math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(a + b + c + 3)
+                    got = np.sum(w * xi[:, 0] ** a * xi[:, 1] ** b * xi[:, 2] ** c)
+                    assert abs(got - exact) < 1e-15
+    else:  # Gauss-Legendre with n points per axis is exact to degree 2n-1 per axis
+        deg = 3 if t == O.HEX8 else 5
+        for a in range(deg + 1):
+            for b in range(deg + 1):
+                for c in range(deg + 1):
+                    one = [2.0 / (k + 1) if k % 2 == 0 else 0.0 for k in (a, b, c)]
+                    got = np.sum(w * xi[:, 0] ** a * xi[:, 1] ** b * xi[:, 2] ** c)
+                    assert abs(got - np.prod(one)) < 1e-13
+
+
+def check_shape_functions(t, rng):
+    nodes = ref_nodes(t)
+    for b, x in enumerate(nodes):  # Kronecker property at the nodes
+        N, _ = O.shape(t, x)
+        assert np.allclose(N, np.eye(len(nodes))[b], atol=1e-14)
+    for _ in range(5):
+        x = rng.uniform(0, 0.3, 3) if t == O.TET4 else rng.uniform(-1, 1, 3)
+        N, dN = O.shape(t, x)
+        assert abs(N.sum() - 1.0) < 1e-14  # partition of unity
+        assert np.allclose(dN.sum(axis=0), 0.0, atol=1e-13)
+        eps = 1e-6
+        for j in range(3):  # derivative against central differences
+            e = np.zeros(3)
+            e[j] = eps
+            fd = (O.shape(t, x + e)[0] - O.shape(t, x - e)[0]) / (2 * eps)
+            assert np.allclose(dN[:, j], fd, atol=1e-8)
+
+
+@pytest.mark.parametrize("t", TYPES)
+def test_quadrature(t):
+    check_quadrature(t)
+
+
+@pytest.mark.parametrize("t", TYPES)
+def test_shape_functions(t):
+    check_shape_functions(t, np.random.default_rng(1))
+
+
+# ------------------------------------------------------------------ closed-form element matrices
+
+def lagrange_1d(nodes):
+    """Lagrange basis polynomials on the given nodes (numpy polynomial coefficients)."""
+    basis = []
+    for i, xi in enumerate(nodes):
+        c = np.array([1.0])
+        for m, xm in enumerate(nodes):
+            if m != i:
+                c = P.polymul(c, np.array([-xm, 1.0]) / (xi - xm))
+        basis.append(c)
+    return basis
+
+
+def matrices_1d(H, order):
+    """Exact 1-D mass, stiffness and convection (int l_a l_b') matrices on [0, H]."""
+    nodes = np.linspace(0.0, H, order + 1)
+    L = lagrange_1d(nodes)
+    dL = [P.polyder(c) for c in L]
+
+    def integ(c):
+        ci = P.polyint(c)
+        return P.polyval(H, ci) - P.polyval(0.0, ci)
+
+    q = order + 1
+    M = np.array([[integ(P.polymul(L[a], L[b])) for b in range(q)] for a in range(q)])
+    K = np.array([[integ(P.polymul(dL[a], dL[b])) for b in range(q)] for a in range(q)])
+    Cv = np.array([[integ(P.polymul(L[a], dL[b])) for b in range(q)] for a in range(q)])
+    return M, K, Cv
+
+
+def box_element(t, H):
+    q = 2 if t == O.HEX8 else 3
+    pts = [np.linspace(0, H[d], q) for d in range(3)]
+    return np.array([[pts[0][i], pts[1][j], pts[2][k]] for k in range(q) for j in range(q) for i in range(q)])
+
+
+def element_terms(t, xe, ue, k, s, phi, dt, terms):
+    nen = xe.shape[0]
+    return O.element(t, xe, ue, np.full(nen, k), np.full(nen, s), phi, dt, terms)
+
+
+def check_box_closed_forms(t):
+    H = (0.7, 1.3, 0.45)  # distinct sides catch axis mix-ups
+    order = 1 if t == O.HEX8 else 2
+    xe = box_element(t, H)
+    nen = xe.shape[0]
+    u = np.array([0.3, -0.8, 0.55])
+    ue = np.tile(u, (nen, 1))
+    phi = np.linspace(0.1, 0.9, nen)
+    m = [matrices_1d(H[d], order) for d in range(3)]
+    Mx, My, Mz = m[0][0], m[1][0], m[2][0]
+    M = np.kron(Mz, np.kron(My, Mx))
+    K = (np.kron(Mz, np.kron(My, m[0][1])) + np.kron(Mz, np.kron(m[1][1], Mx)) + np.kron(m[2][1], np.kron(My, Mx)))
+    Cv = (u[0] * np.kron(Mz, np.kron(My, m[0][2])) + u[1] * np.kron(Mz, np.kron(m[1][2], Mx)) +
+          u[2] * np.kron(m[2][2], np.kron(My, Mx)))
+    scale = np.abs(M).max()
+    A, b = element_terms(t, xe, ue, 0.0, 0.0, phi, 1.0, O.MASS)
+    assert np.allclose(A, M, rtol=0, atol=1e-13 * scale)
+    assert np.allclose(b, M @ phi, rtol=0, atol=1e-13 * scale)
+    A, _ = element_terms(t, xe, ue, 0.37, 0.0, phi, 1.0, O.DIFF)
+    assert np.allclose(A, 0.37 * K, rtol=0, atol=1e-12 * np.abs(K).max())
+    A, _ = element_terms(t, xe, ue, 0.0, 0.0, phi, 1.0, O.CONV)
+    assert np.allclose(A, Cv, rtol=0, atol=1e-12 * np.abs(Cv).max())
+    A, _ = element_terms(t, xe, ue, 0.0, 4.2, phi, 1.0, O.REAC)
+    assert np.allclose(A, 4.2 * M, rtol=0, atol=1e-12 * 4.2 * scale)
+    A, _ = element_terms(t, xe, ue, 0.0, 0.0, phi, 0.25, O.MASS)
+    assert np.allclose(A, M / 0.25, rtol=0, atol=1e-12 * scale / 0.25)
+
+
+def random_tet(rng):
+    while True:
+        x = rng.uniform(-1, 1, (4, 3))
+        if np.linalg.det(np.stack([x[1] - x[0], x[2] - x[0], x[3] - x[0]])) > 0.2:
+            return x
+
+
+def check_tet_closed_forms(rng):
+    xe = random_tet(rng)
+    V = np.linalg.det(np.stack([xe[1] - xe[0], xe[2] - xe[0], xe[3] - xe[0]])) / 6.0
+    # barycentric gradients: rows 1..3 of inv([[1, x_a]]^T)
+    T4 = np.hstack([np.ones((4, 1)), xe])
+    grad = np.linalg.inv(T4)[1:, :].T  # (4, 3): grad lambda_a
+    M = V / 20.0 * (np.ones((4, 4)) + np.eye(4))
+    K = V * grad @ grad.T
+    u = np.array([0.4, -0.2, 0.9])
+    ue = np.tile(u, (4, 1))
+    Cv = (V / 4.0) * np.tile(grad @ u, (4, 1))  # row a, column b: (V/4) u . grad lambda_b
+    phi = np.array([0.2, 0.5, 0.1, 0.9])
+    A, b = element_terms(O.TET4, xe, ue, 0.0, 0.0, phi, 1.0, O.MASS)
+    assert np.allclose(A, M, atol=1e-14) and np.allclose(b, M @ phi, atol=1e-14)
+    A, _ = element_terms(O.TET4, xe, ue, 0.9, 0.0, phi, 1.0, O.DIFF)
+    assert np.allclose(A, 0.9 * K, atol=1e-13)
+    A, _ = element_terms(O.TET4, xe, ue, 0.0, 0.0, phi, 1.0, O.CONV)
+    assert np.allclose(A, Cv, atol=1e-13)
+    A, _ = element_terms(O.TET4, xe, ue, 0.0, 3.0, phi, 1.0, O.REAC)
+    assert np.allclose(A, 3.0 * M, atol=1e-13)
+
+
+@pytest.mark.parametrize("t", (O.HEX8, O.HEX27))
+def test_box_closed_forms(t):
+    check_box_closed_forms(t)
+
+
+def test_tet_closed_forms():
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        check_tet_closed_forms(rng)
+
+
+# ------------------------------------------------------------------ assembled-operator invariants
+
+def small_mesh(t, n, frac, seed=3):
+    mesh = G.structured_mesh(t, n)
+    rng = np.random.default_rng(seed)
+    G.perturb_interior(mesh, rng, frac)
+    return mesh
+
+
+def const_fields(n_node, coords, k=0.0, s=0.0, phi=None, u=None, dt=1.0):
+    vel = np.zeros((3, n_node)) if u is None else (np.tile(np.asarray(u, float)[:, None], (1, n_node))
+                                                   if np.ndim(u) == 1 else u)
+    ph = np.zeros(n_node) if phi is None else phi
+    return G.Fields(vel, np.full((1, n_node), k), np.full((1, n_node), s), ph[None, :].copy(), dt)
+
+
+def csr(mesh, fields, terms):
+    rp, ci, _ = O.pattern(mesh.elem_type, mesh.conn, mesh.n_node, with_pos=False)
+    vals, rhs = O.assemble(mesh.elem_type, mesh.coords, mesh.conn, rp, ci, fields, terms)
+    A = sp.csr_matrix((vals[0], ci, rp), shape=(mesh.n_node, mesh.n_node))
+    return A, rhs[0]
+
+
+INV_MESH = {O.TET4: (3, 0.2), O.HEX8: (3, 0.15), O.HEX27: (2, 0.1)}
+
+
+def check_invariants(t):
+    n, frac = INV_MESH[t]
+    mesh = small_mesh(t, n, frac)
+    N = mesh.n_node
+    rng = np.random.default_rng(11)
+    one = np.ones(N)
+    uvar = G.velocity_field(mesh.coords)
+    kvar = G.Fields(uvar, rng.uniform(0.01, 0.1, (1, N)), rng.uniform(0, 5, (1, N)), rng.uniform(0, 1, (1, N)), 1e-3)
+    # diffusion and convection annihilate constants
+    A, _ = csr(mesh, kvar, O.DIFF)
+    assert np.abs(A @ one).max() < 1e-12 * abs(A).max()
+    A, _ = csr(mesh, kvar, O.CONV)
+    assert np.abs(A @ one).max() < 1e-12 * abs(A).max()
+    # mass matrix entries sum to the volume of the unit cube
+    M, _ = csr(mesh, const_fields(N, mesh.coords), O.MASS)
+    assert abs(M.sum() - 1.0) < 1e-12
+    # symmetry of mass, diffusion, reaction
+    for terms in (O.MASS, O.DIFF, O.REAC):
+        A, _ = csr(mesh, kvar, terms)
+        assert abs(A - A.T).max() < 1e-13 * abs(A).max()
+    # constant state is preserved: s = 0, phi_old = 1 -> A 1 = b
+    f = G.Fields(uvar, kvar.diffusivity, np.zeros((1, N)), np.ones((1, N)), 1e-3)
+    A, b = csr(mesh, f, O.ALL_TERMS)
+    assert np.abs(A @ one - b).max() < 1e-11 * np.abs(b).max()
+    # SUPG sees a zero residual: constant s, phi = c, phi_old = c (1 + s dt)
+    s0, c0, dt = 3.5, 0.7, 1e-3
+    f = G.Fields(uvar, kvar.diffusivity, np.full((1, N), s0), np.full((1, N), c0 * (1 + s0 * dt)), dt)
+    A, b = csr(mesh, f, O.SUPG)
+    assert np.abs(A @ (c0 * one) - b).max() < 1e-11 * np.abs(b).max()
+    # SUPG zero residual for a linear field advected by a constant velocity
+    g, u0 = np.array([0.3, -1.1, 0.6]), np.array([0.8, 0.2, -0.5])
+    phi = mesh.coords @ g + 0.4
+    f = const_fields(N, mesh.coords, k=0.02, s=0.0, phi=phi + dt * (u0 @ g), u=u0, dt=dt)
+    A, b = csr(mesh, f, O.SUPG)
+    assert np.abs(A @ phi - b).max() < 1e-10 * np.abs(b).max()
+    # zero velocity switches SUPG off
+    f0 = G.Fields(np.zeros((3, N)), kvar.diffusivity, kvar.reaction, kvar.phi_old, kvar.dt)
+    A, b = csr(mesh, f0, O.ALL_TERMS)
+    A2, b2 = csr(mesh, f0, O.ALL_TERMS & ~O.SUPG)
+    assert abs(A - A2).max() == 0.0 and np.abs(b - b2).max() == 0.0
+    # the convection term goes with the velocity linearly and the SUPG-free operator is the sum of its terms
+    At, bt = csr(mesh, kvar, O.ALL_TERMS & ~O.SUPG)
+    parts = [csr(mesh, kvar, tm) for tm in (O.MASS, O.CONV, O.DIFF, O.REAC)]
+    assert abs(At - sum(p[0] for p in parts)).max() < 1e-12 * abs(At).max()
+    assert np.abs(bt - parts[0][1]).max() < 1e-13 * np.abs(bt).max()
+
+
+def check_scaling_translation(t):
+    n, frac = INV_MESH[t]
+    mesh = small_mesh(t, n, frac)
+    N = mesh.n_node
+    rng = np.random.default_rng(5)
+    f = G.Fields(np.tile(np.array([[0.5], [0.1], [-0.3]]), (1, N)), rng.uniform(0.01, 0.1, (1, N)),
+                 rng.uniform(0, 5, (1, N)), rng.uniform(0, 1, (1, N)), 1e-2)
+    lam = 2.5
+    big = G.Mesh(t, mesh.coords * lam, mesh.conn, mesh.n_cells, mesh.h * lam)
+    for terms, power in ((O.MASS, 3), (O.REAC, 3), (O.CONV, 2), (O.DIFF, 1)):
+        A, _ = csr(mesh, f, terms)
+        B, _ = csr(big, f, terms)
+        assert abs(B - lam ** power * A).max() < 1e-12 * abs(B).max()
+    moved = G.Mesh(t, mesh.coords + np.array([3.0, -7.0, 11.0]), mesh.conn, mesh.n_cells, mesh.h)
+    A, b = csr(mesh, f, O.ALL_TERMS)
+    B, c = csr(moved, f, O.ALL_TERMS)
+    assert abs(A - B).max() < 1e-10 * abs(A).max() and np.abs(b - c).max() < 1e-10 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("t", TYPES)
+def test_invariants(t):
+    check_invariants(t)
+
+
+@pytest.mark.parametrize("t", TYPES)
+def test_scaling_translation(t):
+    check_scaling_translation(t)
+
+
+# ------------------------------------------------------------------ patch test
+
+def boundary_faces(mesh):
+    """(node list, reference-face kind) of every boundary face of a structured unit-cube mesh."""
+    t = mesh.elem_type
+    if t == O.TET4:
+        faces = {}
+        for e in mesh.conn:
+            for f in ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)):
+                key = tuple(sorted(e[list(f)]))
+                faces[key] = faces.get(key, 0) + 1
+        return [list(k) for k, c in faces.items() if c == 1]
+    q = 2 if t == O.HEX8 else 3
+    out = []
+    for e in mesh.conn:
+        loc = e.reshape(q, q, q)  # [k][j][i]
+        for sl in (loc[0], loc[-1], loc[:, 0, :], loc[:, -1, :], loc[:, :, 0], loc[:, :, -1]):
+            x = mesh.coords[sl.ravel()]
+            on = [np.all(np.abs(x[:, d] - v) < 1e-12) for d in range(3) for v in (0.0, 1.0)]
+            if any(on):
+                out.append(sl)
+    return out
+
+
+def boundary_flux(mesh, kval, g):
+    """f_i = int_dOmega N_i k g.n on the planar faces of the unit cube."""
+    f = np.zeros(mesh.n_node)
+    for face in boundary_faces(mesh):
+        nodes = np.asarray(face).ravel()
+        x = mesh.coords[nodes]
+        c = x.mean(axis=0)
+        d = [d for d in range(3) if np.all(np.abs(x[:, d] - x[0, d]) < 1e-12)][0]
+        n = np.zeros(3)
+        n[d] = 1.0 if x[0, d] > 0.5 else -1.0
+        if mesh.elem_type == O.TET4:
+            area = 0.5 * np.linalg.norm(np.cross(x[1] - x[0], x[2] - x[0]))
+            w = np.full(3, area / 3.0)
+        else:
+            arr = np.asarray(face)
+            q = arr.shape[0]
+            ext = [np.ptp(x[:, dd]) for dd in range(3) if dd != d]
+            area = ext[0] * ext[1]
+            # Simpson (q=3) or trapezoid (q=2) weights integrate the face basis exactly on a flat rectangle
+            w1 = np.array([0.5, 0.5]) if q == 2 else np.array([1.0, 4.0, 1.0]) / 6.0
+            w = (np.outer(w1, w1) * area).ravel()
+        del c
+        f[nodes] += kval * (g @ n) * w
+    return f
+
+
+@pytest.mark.parametrize("t,frac", [(O.TET4, 0.2), (O.HEX8, 0.15), (O.HEX27, 0.0)])
+def test_patch_test(t, frac):
+    check_patch(t, frac)
+
+
+def check_patch(t, frac):
+    n = 3 if t != O.HEX27 else 2
+    mesh = small_mesh(t, n, frac)
+    N = mesh.n_node
+    g = np.array([0.7, -0.4, 1.3])
+    phi = mesh.coords @ g + 0.25
+    kval = 0.3
+    f = const_fields(N, mesh.coords, k=kval)
+    K, _ = csr(mesh, f, O.DIFF)
+    got = K @ phi
+    want = boundary_flux(mesh, kval, g)
+    assert np.abs(got - want).max() < 1e-12 * np.abs(want).max()
+
+
+# ------------------------------------------------------------------ matrix-free, brute force, pattern
+
+def check_matfree(t):
+    n, frac = INV_MESH[t]
+    mesh = small_mesh(t, n, frac)
+    N = mesh.n_node
+    rng = np.random.default_rng(9)
+    f = G.Fields(G.velocity_field(mesh.coords), rng.uniform(0.01, 0.1, (1, N)), rng.uniform(0, 5, (1, N)),
+                 rng.uniform(0, 1, (1, N)), 1e-3)
+    A, _ = csr(mesh, f, O.ALL_TERMS)
+    x = rng.standard_normal(N)
+    y = O.apply(t, mesh.coords, mesh.conn, f, 0, x)
+    assert np.abs(A @ x - y).max() < 1e-12 * np.abs(y).max()
+
+
+def dense_bruteforce(mesh, f, terms):
+    t, N = mesh.elem_type, mesh.n_node
+    A = np.zeros((N, N))
+    b = np.zeros(N)
+    for e in mesh.conn:
+        Ae, be = O.element(t, mesh.coords[e], f.velocity[:, e].T, f.diffusivity[0, e], f.reaction[0, e],
+                           f.phi_old[0, e], f.dt, terms)
+        for a in range(len(e)):
+            b[e[a]] += be[a]
+            for bb in range(len(e)):
+                A[e[a], e[bb]] += Ae[a, bb]
+    return A, b
+
+
+def check_bruteforce(t):
+    rng = np.random.default_rng(21)
+    for n_el in (1, 2, 5, 8):
+        mesh = G.structured_mesh(t, 2)
+        mesh.conn = mesh.conn[rng.permutation(mesh.n_elem)[:n_el]]
+        G.perturb_interior(mesh, rng, 0.1)
+        N = mesh.n_node
+        f = G.Fields(G.velocity_field(mesh.coords), rng.uniform(0.01, 0.1, (1, N)), rng.uniform(0, 5, (1, N)),
+                     rng.uniform(0, 1, (1, N)), 1e-3)
+        A, b = csr(mesh, f, O.ALL_TERMS)
+        D, db = dense_bruteforce(mesh, f, O.ALL_TERMS)
+        assert np.abs(A.toarray() - D).max() < 1e-12 * np.abs(D).max()
+        assert np.abs(b - db).max() < 1e-12 * np.abs(db).max()
+        # pattern = nonzero structure of (node-element incidence)(its transpose), diagonal of used nodes included
+        inc = np.zeros((N, len(mesh.conn)))
+        for i, e in enumerate(mesh.conn):
+            inc[e, i] = 1.0
+        S = (inc @ inc.T) > 0
+        rp, ci, pos = O.pattern(t, mesh.conn, N)
+        P_ = np.zeros((N, N), bool)
+        for r in range(N):
+            P_[r, ci[rp[r]:rp[r + 1]]] = True
+            assert np.all(np.diff(ci[rp[r]:rp[r + 1]]) > 0)
+        assert np.array_equal(S, P_)
+        for e in range(len(mesh.conn)):
+            for a in range(mesh.conn.shape[1]):
+                for bb in range(mesh.conn.shape[1]):
+                    k = pos[e, a, bb]
+                    assert rp[mesh.conn[e, a]] <= k < rp[mesh.conn[e, a] + 1]
+                    assert ci[k] == mesh.conn[e, bb]
+
+
+def kuhn_nnz(n):
+    m = n + 1
+    edges = 3 * n * m * m + 3 * n * n * m + n ** 3  # axis edges + face diagonals + body diagonals
+    return m ** 3 + 2 * edges
+
+
+def tensor_nnz(n, order):
+    m = order * n + 1
+    rows = np.zeros(m, int)
+    for c in range(n):  # 1-D pattern: nodes of one cell are all coupled
+        idx = np.arange(order * c, order * c + order + 1)
+        for i in idx:
+            rows[i] = 0
+    couple = np.zeros((m, m), bool)
+    for c in range(n):
+        idx = np.arange(order * c, order * c + order + 1)
+        couple[np.ix_(idx, idx)] = True
+    return int(couple.sum(axis=1).sum()) ** 3
+
+
+def check_pattern_counts():
+    for n in (2, 4, 10):
+        m = G.structured_mesh(O.TET4, n)
+        rp, ci, _ = O.pattern(O.TET4, m.conn, m.n_node, with_pos=False)
+        assert rp[-1] == kuhn_nnz(n)
+        inner = (n // 2) * (1 + (n + 1) + (n + 1) ** 2)
+        assert rp[inner + 1] - rp[inner] == 15
+    assert kuhn_nnz(10) == 17191 and kuhn_nnz(100) == 15210901
+    for t, order, n, interior in ((O.HEX8, 1, 4, [27]), (O.HEX27, 2, 2, [125, 75, 45, 27])):
+        m = G.structured_mesh(t, n)
+        rp, ci, _ = O.pattern(t, m.conn, m.n_node, with_pos=False)
+        assert rp[-1] == tensor_nnz(n, order)
+        M = order * n + 1
+        rows = np.diff(rp)
+        if t == O.HEX8:
+            assert rows[2 + 2 * M + 2 * M * M] == 27
+        else:  # vertex (2,2,2), edge (1,2,2), face (1,1,2), centre (1,1,1) of the 2x2x2 grid of elements
+            for (i, j, k), want in zip(((2, 2, 2), (1, 2, 2), (1, 1, 2), (1, 1, 1)), interior):
+                assert rows[i + j * M + k * M * M] == want
+    assert tensor_nnz(128, 1) == 57066625 and tensor_nnz(48, 2) == 57066625 and tensor_nnz(256, 1) == 454756609
+
+
+@pytest.mark.parametrize("t", TYPES)
+def test_matfree_equals_spmv(t):
+    check_matfree(t)
+
+
+@pytest.mark.parametrize("t", TYPES)
+def test_bruteforce_small_meshes(t):
+    check_bruteforce(t)
+
+
+def test_pattern_counts():
+    check_pattern_counts()
+
+
+def test_validation_codes():
+    m = G.structured_mesh(O.TET4, 2)
+    assert O.validate(O.TET4, m.coords, m.conn) == O.OK
+    bad = m.conn.copy()
+    bad[3, 1] = m.n_node
+    assert O.validate(O.TET4, m.coords, bad) == O.ERR_RANGE
+    bad = m.conn.copy()
+    bad[3, 1] = bad[3, 2]
+    assert O.validate(O.TET4, m.coords, bad) == O.ERR_DUP
+    bad = m.conn.copy()
+    bad[3, [1, 2]] = bad[3, [2, 1]]
+    assert O.validate(O.TET4, m.coords, bad) == O.ERR_INVERTED
+    h = G.structured_mesh(O.HEX8, 2)
+    bad = h.conn.copy()
+    bad[0, [0, 1]] = bad[0, [1, 0]]
+    assert O.validate(O.HEX8, h.coords, bad) == O.ERR_INVERTED
+
+
+# ------------------------------------------------------------------ planted mistakes
+
+def all_pins():
+    rng = np.random.default_rng(1)
+    pins = []
+    for t in TYPES:
+        pins += [lambda t=t: check_quadrature(t), lambda t=t: check_shape_functions(t, rng),
+                 lambda t=t: check_invariants(t), lambda t=t: check_matfree(t),
+                 lambda t=t: check_scaling_translation(t)]
+    pins += [lambda: check_box_closed_forms(O.HEX8), lambda: check_box_closed_forms(O.HEX27),
+             lambda: check_tet_closed_forms(np.random.default_rng(7)), check_pattern_counts,
+             lambda: check_patch(O.TET4, 0.2), lambda: check_patch(O.HEX8, 0.15), lambda: check_patch(O.HEX27, 0.0),
+             lambda: check_bruteforce(O.HEX8)]
+    return pins
+
+
+MUTATIONS = {
+    1: "diffusion term dropped",
+    2: "convection sign flipped",
+    3: "convection operands transposed",
+    4: "physical gradient uses J^-1 instead of J^-T",
+    5: "wrong tetrahedron quadrature weight",
+    6: "SUPG part of the RHS dropped",
+    7: "reaction term dropped from the SUPG residual",
+    8: "diagonal missing from the pattern",
+    9: "element matrix scattered transposed",
+    10: "mass term uses N_a N_a",
+    11: "quadratic 1-D nodes in the wrong order",
+}
+
+
+@pytest.mark.parametrize("m", sorted(MUTATIONS))
+def test_pins_catch_planted_mistakes(m):
+    failed = 0
+    with O.mutation(m):
+        for pin in all_pins():
+            try:
+                pin()
+            except (AssertionError, ValueError):
+                failed += 1
+    assert failed > 0, f"no pin caught mutation {m}: {MUTATIONS[m]}"
