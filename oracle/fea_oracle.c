@@ -195,8 +195,18 @@ static void inverse3(double J[3][3], double det, double Ji[3][3]) {
 /* Element matrix Ae[a*nen+b] and RHS be[a] of one equation from gathered nodal
  * data: xe[a*3+i] coordinates, ue[a*3+i] velocity, ke/se/phie nodal diffusivity,
  * reaction and previous-step values.  Only the terms in `terms` are added. */
+static int element_impl(int type, const double* xe, const double* ue, const double* ke, const double* se,
+                        const double* phie, double dt, int terms, double* Ae, double* be, double* babs);
+
 int or_element(int type, const double* xe, const double* ue, const double* ke, const double* se,
                const double* phie, double dt, int terms, double* Ae, double* be) {
+  return element_impl(type, xe, ue, ke, se, phie, dt, terms, Ae, be, NULL);
+}
+
+/* As or_element; babs[a] (if not NULL) receives sum_g |dV (N_a + tau u.grad N_a) phi_g / dt| over the
+ * included RHS terms: the magnitude of the summands of b_a, which bounds its rounding error. */
+static int element_impl(int type, const double* xe, const double* ue, const double* ke, const double* se,
+                        const double* phie, double dt, int terms, double* Ae, double* be, double* babs) {
   int nen = or_nen(type);
   if (!nen || dt <= 0.0) return OR_ERR_ARG;
   double xq[MAXN * 3], wq[MAXN];
@@ -225,6 +235,8 @@ int or_element(int type, const double* xe, const double* ue, const double* ke, c
 
   for (int i = 0; i < nen * nen; ++i) Ae[i] = 0.0;
   for (int a = 0; a < nen; ++a) be[a] = 0.0;
+  if (babs)
+    for (int a = 0; a < nen; ++a) babs[a] = 0.0;
 
   for (int g = 0; g < ng; ++g) {
     const double* Ng = N[g];
@@ -272,6 +284,11 @@ int or_element(int type, const double* xe, const double* ue, const double* ke, c
       for (int a = 0; a < nen; ++a) be[a] += w * Ng[a] * pg / dt;
     if ((terms & OR_SUPG) && g_mutation != 6)
       for (int a = 0; a < nen; ++a) be[a] += w * tau * ua[a] * pg / dt;
+    if (babs)
+      for (int a = 0; a < nen; ++a) {
+        if (terms & OR_MASS) babs[a] += fabs(w * Ng[a] * pg / dt);
+        if (terms & OR_SUPG) babs[a] += fabs(w * tau * ua[a] * pg / dt);
+      }
   }
   return OR_OK;
 }
@@ -441,7 +458,8 @@ static int64_t find_col(const int64_t* rowptr, const int32_t* colind, int32_t r,
 
 /* Assemble elements [e_begin, e_end) of all n_eq equations into values[n_eq][nnz]
  * and rhs[n_eq][n_node] (added to what is there), plus optional abs-sum
- * denominators absA[n_eq][nnz] = sum_e |A^e_ij| and absb[n_eq][n_node].
+ * denominators absA[n_eq][nnz] = sum_e |A^e_ij| and absb[n_eq][n_node] = the sum over elements and
+ * Gauss points of the magnitudes of the summands of b_i (cancellation inside one element counts too).
  * Element loop outermost, plain `+=` in element order (Sec. 4.2). */
 int or_assemble(int type, const double* coords, int64_t n_node, const int32_t* conn, int64_t e_begin,
                 int64_t e_end, const int64_t* rowptr, const int32_t* colind, int64_t nnz, const double* vel,
@@ -449,12 +467,12 @@ int or_assemble(int type, const double* coords, int64_t n_node, const int32_t* c
                 double* values, double* rhs, double* absA, double* absb) {
   int nen = or_nen(type);
   if (!nen || n_eq <= 0) return OR_ERR_ARG;
-  double xe[MAXN * 3], ue[MAXN * 3], ke[MAXN], se[MAXN], pe[MAXN], Ae[MAXN * MAXN], be[MAXN];
+  double xe[MAXN * 3], ue[MAXN * 3], ke[MAXN], se[MAXN], pe[MAXN], Ae[MAXN * MAXN], be[MAXN], bab[MAXN];
   for (int64_t e = e_begin; e < e_end; ++e) {
     const int32_t* ce = conn + e * nen;
     for (int q = 0; q < n_eq; ++q) {
       gather(nen, ce, coords, n_node, vel, kd, sr, phi, q, xe, ue, ke, se, pe);
-      int st = or_element(type, xe, ue, ke, se, pe, dt, terms, Ae, be);
+      int st = element_impl(type, xe, ue, ke, se, pe, dt, terms, Ae, be, bab);
       if (st) return st;
       for (int a = 0; a < nen; ++a) {
         for (int b = 0; b < nen; ++b) {
@@ -466,7 +484,7 @@ int or_assemble(int type, const double* coords, int64_t n_node, const int32_t* c
           if (absA) absA[(int64_t)q * nnz + k] += fabs(Ae[a * nen + b]);
         }
         rhs[(int64_t)q * n_node + ce[a]] += be[a];
-        if (absb) absb[(int64_t)q * n_node + ce[a]] += fabs(be[a]);
+        if (absb) absb[(int64_t)q * n_node + ce[a]] += bab[a];
       }
     }
   }
@@ -491,7 +509,7 @@ int64_t or_row(int type, const double* coords, int64_t n_node, const int32_t* co
     rhs[q] = 0.0;
     absr[q] = 0.0;
   }
-  double xe[MAXN * 3], ue[MAXN * 3], ke[MAXN], se[MAXN], pe[MAXN], Ae[MAXN * MAXN], be[MAXN];
+  double xe[MAXN * 3], ue[MAXN * 3], ke[MAXN], se[MAXN], pe[MAXN], Ae[MAXN * MAXN], be[MAXN], bab[MAXN];
   for (int64_t t = inc_ptr[r]; t < inc_ptr[r + 1]; ++t) {
     int64_t e = inc_elem[t];
     const int32_t* ce = conn + e * nen;
@@ -499,7 +517,7 @@ int64_t or_row(int type, const double* coords, int64_t n_node, const int32_t* co
     while (ce[a] != r) ++a;
     for (int q = 0; q < n_eq; ++q) {
       gather(nen, ce, coords, n_node, vel, kd, sr, phi, q, xe, ue, ke, se, pe);
-      int st = or_element(type, xe, ue, ke, se, pe, dt, terms, Ae, be);
+      int st = element_impl(type, xe, ue, ke, se, pe, dt, terms, Ae, be, bab);
       if (st) return -st;
       for (int b = 0; b < nen; ++b) {
         int64_t k = 0;
@@ -509,7 +527,7 @@ int64_t or_row(int type, const double* coords, int64_t n_node, const int32_t* co
         absv[q * cap + k] += fabs(Ae[a * nen + b]);
       }
       rhs[q] += be[a];
-      absr[q] += fabs(be[a]);
+      absr[q] += bab[a];
     }
   }
   return nc;
