@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Throughput of batched FP32 finite-element assembly of CDR transport equations.
+
+One step = one fea_assemble call over the whole workload: gather, Gauss-point
+geometry, per-equation coefficients, element matrices and RHS, scatter into the
+CSR values and RHS of every equation.  Inputs are resident in HBM; the inputs
+plus outputs of every workload are larger than the 129 MB L2, so no L2 flush is
+needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+instead (a bounded sample of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2107_11541_gb300 import meshgen as G  # noqa: E402
+
+WORKLOADS = {"tet4_100_perm_1eq": 1, "hex8_128_21eq": 2, "hex27_48_11eq": 3, "hex8_256_32eq": 4}
+DEFAULT_WORKLOAD = "hex8_128_21eq"
+METRIC = "elements x equations assembled per second (FP32 batched)"
+UNIT = "elem*eq/s"
+HBM_PEAK_FALLBACK = 6800.0
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+NEN = {G.TET4: 4, G.HEX8: 8, G.HEX27: 27}
+
+
+def algorithmic_bytes(E, N, nnz, nen, q, s=4):
+    """conn + coordinates and velocity + per-equation k, s, phi + values and RHS written once."""
+    return 4 * E * nen + 6 * N * s + 3 * q * N * s + q * (nnz + N) * s
+
+
+def algorithmic_flops_per_elem_eq(nen):
+    """Multiply-adds of the operator in its direct form, per element and equation: the rank-NG
+    Galerkin/SUPG product (NG NEN^2), the symmetric diffusion sum (NG NEN(NEN+1)/2) and the
+    interpolation/test-function/RHS vectors (6 NG NEN); NG = NEN for all three element types."""
+    ng = nen
+    return 2 * (ng * nen * nen + ng * nen * (nen + 1) // 2 + 6 * ng * nen)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2107_11541_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_digest") != kernel_source_digest():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def make(workload: str):
+    idx = WORKLOADS[workload]
+    w = G.make_workload(idx)
+    return w
+
+
+def cpu_oracle_sample(w, budget_s: float):
+    """Oracle throughput on the first elements of the workload (all equations), single thread."""
+    import oracle as O
+    m, f = w.mesh, w.fields.astype(np.float32).astype(np.float64)
+    rp, ci, _ = O.pattern(m.elem_type, m.conn, m.n_node, with_pos=False)
+    q = f.n_eq
+    t0 = time.perf_counter()
+    n0 = 64 if m.elem_type == G.HEX27 else 512
+    O.assemble(m.elem_type, m.coords, m.conn, rp, ci, f, e_range=(0, n0))
+    rate = n0 / max(time.perf_counter() - t0, 1e-9)
+    ne = int(min(m.n_elem, max(n0, rate * budget_s)))
+    t0 = time.perf_counter()
+    O.assemble(m.elem_type, m.coords, m.conn, rp, ci, f, e_range=(0, ne))
+    dt = time.perf_counter() - t0
+    return ne, q, dt, (rp, ci)
+
+
+def run_reference(args, w, rank):
+    if rank != 0:
+        return
+    import oracle as O
+    m = w.mesh
+    f = w.fields.astype(np.float32).astype(np.float64)
+    rp, ci, _ = O.pattern(m.elem_type, m.conn, m.n_node, with_pos=False)
+    q = f.n_eq
+    t0 = time.perf_counter()
+    n0 = 64 if m.elem_type == G.HEX27 else 512
+    O.assemble(m.elem_type, m.coords, m.conn, rp, ci, f, e_range=(0, n0))
+    rate = n0 / max(time.perf_counter() - t0, 1e-9)
+    per_step = max(4.0, 150.0 / max(1, args.steps + args.warmup))
+    ne = int(min(m.n_elem, max(n0, rate * per_step)))
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.assemble(m.elem_type, m.coords, m.conn, rp, ci, f, e_range=(0, ne))
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = ne * q / t
+    sample = f"elements [0, {ne}) of {m.n_elem}, all {q} equations, per step"
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_dict(args.workload, w, None),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_dict(workload, w, nnz):
+    m = w.mesh
+    return {"workload": workload, "elem_type": G.NAMES[m.elem_type], "elements": m.n_elem, "nodes": m.n_node,
+            "nnz": nnz, "n_eq": w.fields.n_eq, "precision": "f32_fused",
+            "l2": "no flush: inputs + outputs per step exceed the 129 MB L2"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--scatter", type=int, default=0, help="0 auto, 1 atomic, 2 row-owned")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    w = make(args.workload)
+    if args.impl == "reference":
+        run_reference(args, w, rank)
+        return
+
+    import torch
+    from paper_2107_11541_gb300 import fea
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    m, fld = w.mesh, w.fields
+    q = fld.n_eq
+    stream = torch.cuda.Stream()
+    h = fea.fea_mesh_create(m.coords, m.conn, m.elem_type, stream)
+    p = fea.fea_pattern_build(h)
+    nnz = fea.fea_pattern_get(p)[3]
+    f32 = fld.astype(np.float32)
+    with torch.cuda.stream(stream):
+        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda(non_blocking=False)
+               for a in (f32.velocity, f32.diffusivity, f32.reaction, f32.phi_old)]
+        values = torch.empty((q, nnz), dtype=torch.float32, device="cuda")
+        rhs = torch.empty((q, m.n_node), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    opts = fea.fea_default_opts(scatter=args.scatter)
+
+    def step(ev=None):
+        if ev is not None:
+            opts.event_begin, opts.event_end = ev[0].cuda_event, ev[1].cuda_event
+        else:
+            opts.event_begin = opts.event_end = None
+        fea.fea_assemble(h, p, *dev, fld.dt, q, opts, values, rhs)
+
+    for _ in range(args.warmup):
+        step()
+    fea.fea_sync(h)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in kev:  # torch creates the CUDA events lazily, on first record
+        a.record(stream)
+        b.record(stream)
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = fea.fea_kernel_launches()
+    clocks.start()
+    time.sleep(0.3)
+    t0e.record(stream)
+    for s in range(args.steps):
+        step(kev[s])
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = fea.fea_kernel_launches() - launches0
+    fea.fea_sync(h)
+    ms = t0e.elapsed_time(t1e) / args.steps
+    kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms, kernel_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, kernel_ms = float(t[0]), float(t[1])
+    units = m.n_elem * q * world
+    value = units / (ms * 1e-3)
+
+    # roofline of the dominant kernel
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else HBM_PEAK_FALLBACK
+    nen = NEN[m.elem_type]
+    abytes = algorithmic_bytes(m.n_elem, m.n_node, nnz, nen, q)
+    aflops = algorithmic_flops_per_elem_eq(nen) * m.n_elem * q
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    hbm_ach = abytes / (kernel_ms * 1e-3) / 1e9
+    alu_ach = aflops / (kernel_ms * 1e-3) / 1e12
+    t_hbm, t_alu = abytes / (hbm_peak * 1e9), aflops / (alu_peak * 1e12)
+    hbm_obj = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
+               "traffic": profiled_traffic(args.workload), "algorithmic_bytes": abytes,
+               "peak_source": "measured" if peaks else "fallback"}
+    alu_obj = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+               "traffic": hbm_obj["traffic"], "algorithmic_flops": aflops,
+               "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    roof, other = (alu_obj, hbm_obj) if t_alu > t_hbm else (hbm_obj, alu_obj)
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args.workload, w, nnz),
+           "clocks": clk, "gpu_launches": int(launches), "kernel_ms": kernel_ms, "roofline": roof,
+           "roofline_other": other}
+
+    if rank == 0 and not args.no_parity:
+        out["parity"] = sampled_parity(w, values, rhs, p, nnz)
+
+    if not args.no_f64 and rank == 0:
+        q64 = q if m.n_elem * q <= 60_000_000 else 4
+        d64 = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+               for a in (fld.velocity, fld.diffusivity[:q64], fld.reaction[:q64], fld.phi_old[:q64])]
+        del values
+        v64 = torch.empty((q64, nnz), dtype=torch.float64, device="cuda")
+        r64 = torch.empty((q64, m.n_node), dtype=torch.float64, device="cuda")
+        o64 = fea.fea_default_opts(precision=fea.FEA_F64_PLAIN)
+        fea.fea_assemble(h, p, *d64, fld.dt, q64, o64, v64, r64)
+        fea.fea_sync(h)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fea.fea_assemble(h, p, *d64, fld.dt, q64, o64, v64, r64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b)
+        v_f64 = m.n_elem * q64 / (t64 * 1e-3)
+        out["fp64_plain"] = {"value": v_f64, "unit": UNIT, "ms_per_step": t64, "equations_timed": q64,
+                             "speedup_f32_fused": value / world / v_f64}
+        del v64, r64, d64
+        values = torch.empty((q, nnz), dtype=torch.float32, device="cuda")
+
+    if not args.no_e2e:
+        out["e2e"] = end_to_end(h, p, f32, m, nnz, q, stream, min(args.steps, 5), world, dist)
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ne, qq, dt, _ = cpu_oracle_sample(w, args.cpu_budget)
+        out["cpu_baseline"] = {"value": ne * qq / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"elements [0, {ne}) of {m.n_elem}, all {qq} equations, FP64 C oracle, "
+                                         f"single thread"}
+    fea.fea_pattern_destroy(p)
+    fea.fea_mesh_destroy(h)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def sampled_parity(w, values, rhs, p, nnz, n_rows=48, seed=5):
+    """Sampled full-size rows against the oracle (computed row by row from incident elements)."""
+    import oracle as O
+    from paper_2107_11541_gb300 import fea
+    m = w.mesh
+    rp_t, ci_t, _ = fea.pattern_tensors(p, m.n_node, 0, NEN[m.elem_type])
+    rp = rp_t.cpu().numpy()
+    rs = O.RowSampler(m.elem_type, m.coords, m.conn, w.fields.astype(np.float32).astype(np.float64))
+    rng = np.random.default_rng(seed)
+    rows = np.unique(np.concatenate([[0, m.n_node - 1], rng.integers(0, m.n_node, n_rows)]))
+    worst_a = worst_b = 0.0
+    for r in rows:
+        cols, ref, _, refb, absb = rs.row(r)
+        k0, k1 = rp[r], rp[r + 1]
+        assert np.array_equal(ci_t[k0:k1].cpu().numpy(), cols)
+        got = values[:, k0:k1].double().cpu().numpy()
+        ea = np.sqrt(((got - ref) ** 2).sum(axis=1) / (ref ** 2).sum(axis=1)).max()
+        gb = rhs[:, r].double().cpu().numpy()
+        eb = (np.abs(gb - refb) / np.where(absb > 0, absb, 1.0)).max()
+        worst_a, worst_b = max(worst_a, ea), max(worst_b, eb)
+    return {"rows": int(len(rows)), "max_row_err_A": worst_a, "max_err_b": worst_b, "tol": 1e-5,
+            "pass": bool(worst_a <= 1e-5 and worst_b <= 1e-5)}
+
+
+def end_to_end(h, p, f32, m, nnz, q, stream, steps, world, dist):
+    """Same metric through fea_assemble_host: pinned host inputs copied in, values and RHS read back."""
+    import torch
+    from paper_2107_11541_gb300 import fea
+    pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+           for a in (f32.velocity, f32.diffusivity, f32.reaction, f32.phi_old)]
+    hv = torch.empty((q, nnz), dtype=torch.float32).pin_memory()
+    hr = torch.empty((q, m.n_node), dtype=torch.float32).pin_memory()
+    opts = fea.fea_default_opts()
+    fea.fea_assemble_host(h, p, *pin, f32.dt, q, opts, hv, hr)
+    times = []
+    for _ in range(steps):
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        fea.fea_assemble_host(h, p, *pin, f32.dt, q, opts, hv, hr)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    if dist is not None:
+        tt = torch.tensor([t], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt[0])
+    h2d = sum(x.numel() * 4 for x in pin)
+    d2h = (hv.numel() + hr.numel()) * 4
+    return {"value": m.n_elem * q * world / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": t * 1e3}
+
+
+if __name__ == "__main__":
+    main()

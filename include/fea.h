@@ -1,0 +1,187 @@
+/*
+ * fea.h -- C ABI of the GB300 finite-element assembly library.
+ *
+ * The library assembles convection-diffusion-reaction (CDR) transport equations
+ * (species mass fractions, enthalpy) element by element on an unstructured mesh
+ * into one shared CSR pattern, on one GPU.  The paper it follows is
+ * "Performance assessment of CUDA and OpenACC in large scale combustion
+ * simulations" (arXiv 2107.11541):
+ *   - Sec. 4.2, Listing 1: the element loop (outer loop over elements, inner
+ *     loop over Gauss points and node pairs building the element matrix Ae from
+ *     shape functions N and the Jacobian weight Jac(g) = w_g det J_g);
+ *   - Sec. 4.2: the assembled matrix is stored in CSR;
+ *   - Sec. 2 and Table 1: heat and species equations, whose matrix assembly is
+ *     most of the time step;
+ *   - Sec. 4.3, Fig. 3: elements grouped by type and packed in fixed-size
+ *     packs with zero padding (see fea_pack_plan).
+ * The paper does not write the transport equations.  The operator assembled is
+ * the backward-Euler Galerkin + SUPG discretisation of
+ *     d(phi)/dt + u.grad(phi) - div(k grad(phi)) + s phi = 0,
+ * per Gauss point g with dV = w_g det J_g:
+ *     A_ab += dV [ N_a N_b/dt + N_a u.grad N_b + k grad N_a.grad N_b + s N_a N_b
+ *                  + tau (u.grad N_a)(N_b/dt + u.grad N_b + s N_b) ]
+ *     b_a  += dV (N_a + tau u.grad N_a) phi_old / dt
+ * with u, k, s, phi_old interpolated from nodal values, tau = 1/(4k/h^2 + 2|u|/h + s)
+ * (0 if the denominator is 0) and h = V_e^(1/3)/p.
+ *
+ * Conventions common to every call
+ *   - All calls return fea_status and never abort or trap.  On failure
+ *     fea_last_error() returns a thread-local message.
+ *   - Node ids are 0-based int32.  Local node order: Tet4 positively oriented
+ *     ((x1-x0)x(x2-x0).(x3-x0) > 0); Hex8 a = i + 2j + 4k and Hex27
+ *     a = i + 3j + 9k, with i, j, k the node's position along xi, eta, zeta.
+ *   - Device work is ordered on the mesh's CUDA stream.  Calls that only
+ *     enqueue work return without waiting; device-detected errors are
+ *     reported by the next call that waits (fea_sync, fea_pattern_build,
+ *     fea_mesh_create) as FEA_ERR_* codes.
+ *   - Array layouts are row-major C arrays; "[a][b]" means b is fastest.
+ */
+#ifndef FEA_H
+#define FEA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FEA_API __attribute__((visibility("default")))
+#else
+#define FEA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fea_mesh fea_mesh;
+typedef struct fea_pattern fea_pattern;
+
+typedef enum { FEA_TET4 = 0, FEA_HEX8 = 1, FEA_HEX27 = 2 } fea_elem_t;
+
+typedef enum {
+  FEA_OK = 0,
+  FEA_ERR_ARG = 1,        /* bad argument: null pointer, negative size, unknown enum, n_eq <= 0, dt <= 0 */
+  FEA_ERR_RANGE = 2,      /* a connectivity entry is outside [0, n_node) */
+  FEA_ERR_DUP_NODE = 3,   /* a node appears twice in one element */
+  FEA_ERR_INVERTED = 4,   /* det J <= 0 at a Gauss point or a corner of an element */
+  FEA_ERR_TOO_LARGE = 5,  /* a size exceeds an index type: nnz >= 2^31, n_node >= 2^31, or a row too long */
+  FEA_ERR_OOM = 6,        /* device or host allocation failed */
+  FEA_ERR_CUDA = 7,       /* a CUDA runtime call failed */
+  FEA_ERR_TIMEOUT = 8,    /* a bounded device-side wait gave up */
+  FEA_ERR_STATE = 9       /* object used in the wrong state (e.g. pattern of another mesh) */
+} fea_status;
+
+typedef enum {
+  FEA_F64_PLAIN = 0,  /* double fields and outputs; one launch per equation, geometry recomputed each time */
+  FEA_F32_FUSED = 1   /* float fields and outputs; all equations in one launch sharing the geometry */
+} fea_precision;
+
+enum {
+  FEA_TERM_MASS = 1,  /* N_a N_b / dt, and the Galerkin RHS N_a phi_old / dt */
+  FEA_TERM_CONV = 2,  /* N_a u.grad N_b */
+  FEA_TERM_DIFF = 4,  /* k grad N_a . grad N_b */
+  FEA_TERM_REAC = 8,  /* s N_a N_b */
+  FEA_TERM_SUPG = 16, /* tau (u.grad N_a)(N_b/dt + u.grad N_b + s N_b), and its RHS part */
+  FEA_TERM_ALL = 31
+};
+
+typedef enum {
+  FEA_SCATTER_AUTO = 0,     /* pick per element type and size (autotuned) */
+  FEA_SCATTER_ATOMIC = 1,   /* element-parallel, atomic adds into zeroed outputs */
+  FEA_SCATTER_ROWOWNED = 2  /* rows accumulated in shared memory and written once (deterministic) */
+} fea_scatter;
+
+typedef struct {
+  int32_t precision;        /* fea_precision, default FEA_F32_FUSED */
+  int32_t terms;            /* bit mask of FEA_TERM_*, default FEA_TERM_ALL */
+  int32_t scatter;          /* fea_scatter, default FEA_SCATTER_AUTO */
+  int32_t accumulate;       /* 0: overwrite values/rhs (default); 1: add to them */
+  double kappa_threshold;   /* F32 path: elements whose Jacobian condition estimate exceeds this get FP64
+                               geometry (default 1e3) */
+  void* event_begin;        /* optional cudaEvent_t recorded on the mesh stream just before the assembly
+                               kernel(s), after any output zeroing; NULL = none */
+  void* event_end;          /* optional cudaEvent_t recorded just after the assembly kernel(s) */
+  int32_t reserved[4];
+} fea_assemble_opts;
+
+/* Fills *opts with the defaults listed above. */
+FEA_API fea_status fea_default_opts(fea_assemble_opts* opts);
+
+/*
+ * fea_mesh_create -- copy a mesh to the device and validate it.
+ *   coords  [n_node][3] double, host or device pointer (detected), copied.
+ *   conn    [n_elem][nen] int32, host or device pointer (detected), copied.
+ *   stream  cudaStream_t used for all work on this mesh (NULL = legacy default stream).
+ *   *out    receives the mesh, owned by the caller, released with fea_mesh_destroy.
+ * Checks (on the device, writing a status word; never traps): ids in range
+ * (FEA_ERR_RANGE), no repeated node in an element (FEA_ERR_DUP_NODE), det J > 0
+ * at every Gauss point and corner (FEA_ERR_INVERTED).  Waits for the stream.
+ * n_elem = 0 is allowed (an empty mesh assembles to the mass-free zero matrix).
+ */
+FEA_API fea_status fea_mesh_create(const double* coords, int64_t n_node, const int32_t* conn, int64_t n_elem,
+                           fea_elem_t type, void* stream, fea_mesh** out);
+FEA_API fea_status fea_mesh_destroy(fea_mesh* mesh);
+/* Rebinds the mesh (and its patterns) to another stream. */
+FEA_API fea_status fea_mesh_set_stream(fea_mesh* mesh, void* stream);
+/* Waits for the mesh's stream and returns any error the device recorded. */
+FEA_API fea_status fea_sync(fea_mesh* mesh);
+
+/*
+ * fea_pattern_build -- the CSR sparsity pattern of the mesh (Sec. 4.2: CSR storage).
+ * Row i holds column j iff some element contains both nodes i and j (j = i
+ * included); columns ascend.  Also builds the position map
+ * pos[e][a][b] = the index k in row conn[e][a] with colind[k] = conn[e][b], and
+ * the internal schedules the assembly kernels use.  All results stay on the
+ * device and are owned by the pattern.  Fails with FEA_ERR_TOO_LARGE when
+ * nnz >= 2^31.  Waits for the stream.
+ */
+FEA_API fea_status fea_pattern_build(fea_mesh* mesh, fea_pattern** out);
+/* Borrowed device pointers: rowptr int64[n_node+1], colind int32[nnz], pos int32[n_elem][nen][nen]. */
+FEA_API fea_status fea_pattern_get(const fea_pattern* pattern, const int64_t** rowptr, const int32_t** colind,
+                           const int32_t** pos, int64_t* nnz);
+FEA_API fea_status fea_pattern_destroy(fea_pattern* pattern);
+
+/*
+ * fea_assemble -- assemble n_eq CDR equations sharing one mesh and pattern.
+ * All array arguments are DEVICE pointers owned by the caller, of element type
+ * double for FEA_F64_PLAIN and float for FEA_F32_FUSED:
+ *   velocity    [3][n_node]     nodal velocity, shared by all equations (SoA)
+ *   diffusivity [n_eq][n_node]  nodal k per equation
+ *   reaction    [n_eq][n_node]  nodal s per equation
+ *   phi_old     [n_eq][n_node]  previous-step nodal values per equation
+ *   values      [n_eq][nnz]     output: CSR values, one standalone matrix per equation
+ *   rhs         [n_eq][n_node]  output: right-hand sides
+ * dt > 0 is the time step; opts may be NULL for the defaults.  Enqueued on the
+ * mesh's stream; returns without waiting.
+ */
+FEA_API fea_status fea_assemble(fea_mesh* mesh, const fea_pattern* pattern, const void* velocity,
+                        const void* diffusivity, const void* reaction, const void* phi_old, double dt,
+                        int32_t n_eq, const fea_assemble_opts* opts, void* values, void* rhs);
+
+/*
+ * fea_assemble_host -- the same operation on HOST arrays (same shapes and
+ * types as fea_assemble).  Copies the inputs to a device workspace owned by the
+ * pattern, assembles, copies values and rhs back, and waits for completion.
+ * Pinned host memory gives the fastest copies.
+ */
+FEA_API fea_status fea_assemble_host(fea_mesh* mesh, const fea_pattern* pattern, const void* velocity,
+                             const void* diffusivity, const void* reaction, const void* phi_old, double dt,
+                             int32_t n_eq, const fea_assemble_opts* opts, void* values, void* rhs);
+
+/*
+ * fea_pack_plan -- the element-pack layout of Sec. 4.3 / Fig. 3: elements of
+ * each type are grouped, then cut into packs of vector_size elements, the last
+ * pack zero-padded.  For n_types counts, writes packs[t] and pads[t].  Host only.
+ */
+FEA_API fea_status fea_pack_plan(const int64_t* count_by_type, int32_t n_types, int32_t vector_size, int64_t* packs,
+                         int64_t* pads);
+
+/* Thread-local message describing the last failure of a call on this thread. */
+FEA_API const char* fea_last_error(void);
+/* Number of CUDA kernels this library has launched in this process so far. */
+FEA_API int64_t fea_kernel_launches(void);
+/* Library version, major*10000 + minor*100 + patch. */
+FEA_API int32_t fea_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FEA_H */

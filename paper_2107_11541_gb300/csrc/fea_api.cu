@@ -1,0 +1,659 @@
+// fea_api.cu -- C ABI entry points, mesh upload and validation, CSR pattern
+// build on the device (Sec. 4.2: CSR storage of the assembled matrix).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <climits>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "fea_internal.cuh"
+#include "fea_plan.cuh"
+
+namespace fea {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+fea_status fail(fea_status st, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+fea_status status_to_error(uint32_t bits) {
+  if (bits & ST_RANGE) return fail(FEA_ERR_RANGE, "connectivity holds a node id outside [0, n_node)");
+  if (bits & ST_DUP) return fail(FEA_ERR_DUP_NODE, "an element lists the same node twice");
+  if (bits & ST_INVERTED) return fail(FEA_ERR_INVERTED, "an element has det J <= 0 at a Gauss point or corner");
+  if (bits & ST_ROW_TOO_LONG) return fail(FEA_ERR_TOO_LARGE, "a node touches too many elements (row candidate list over limit)");
+  if (bits & ST_TIMEOUT) return fail(FEA_ERR_TIMEOUT, "a bounded device-side wait gave up");
+  if (bits & ST_SCHEDULE) return fail(FEA_ERR_STATE, "row-owned schedule does not match the mesh");
+  return FEA_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------------ small device helpers
+
+static constexpr int SCAN_THREADS = 256;
+static constexpr int SCAN_ITEMS = 8;
+static constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Block-wide exclusive scan of SCAN_TILE int64 items held 8 per thread.
+__device__ int64_t block_exclusive_scan(int64_t v[SCAN_ITEMS], int64_t* sh) {
+  int64_t tsum = 0;
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    int64_t x = v[i];
+    v[i] = tsum;
+    tsum += x;
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int64_t incl = tsum;
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) sh[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    int64_t s = lane < SCAN_THREADS / 32 ? sh[lane] : 0;
+    int64_t si = s;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += y;
+    }
+    if (lane < SCAN_THREADS / 32) sh[lane] = si - s;
+    if (lane == SCAN_THREADS / 32 - 1) sh[SCAN_THREADS / 32] = si;
+  }
+  __syncthreads();
+  int64_t off = sh[w] + incl - tsum;
+  for (int i = 0; i < SCAN_ITEMS; ++i) v[i] += off;
+  int64_t total = sh[SCAN_THREADS / 32];
+  __syncthreads();
+  return total;
+}
+
+template <typename TIn>
+__global__ void k_tile_sums(const TIn* in, int64_t n, int64_t* tile_sums) {
+  __shared__ int64_t sh[SCAN_THREADS / 32 + 1];
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  int64_t v[SCAN_ITEMS];
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
+    v[i] = idx < n ? (int64_t)in[idx] : 0;
+  }
+  int64_t total = block_exclusive_scan(v, sh);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Exclusive scan of the tile sums in one block (loops over chunks).
+__global__ void k_scan_tile_sums(int64_t* sums, int64_t n) {
+  __shared__ int64_t sh[SCAN_THREADS / 32 + 1];
+  int64_t carry = 0;
+  for (int64_t base = 0; base < n; base += SCAN_TILE) {
+    int64_t v[SCAN_ITEMS];
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
+      v[i] = idx < n ? sums[idx] : 0;
+    }
+    int64_t total = block_exclusive_scan(v, sh);
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+      int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
+      if (idx < n) sums[idx] = v[i] + carry;
+    }
+    carry += total;
+    __syncthreads();
+  }
+}
+
+// out[i] = sum_{j<i} in[j] for i in [0, n], out has n+1 entries.
+template <typename TIn>
+__global__ void k_scan_apply(const TIn* in, int64_t n, const int64_t* tile_offsets, int64_t* out) {
+  __shared__ int64_t sh[SCAN_THREADS / 32 + 1];
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  int64_t v[SCAN_ITEMS];
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
+    v[i] = idx < n ? (int64_t)in[idx] : 0;
+  }
+  int64_t total = block_exclusive_scan(v, sh);
+  int64_t off = tile_offsets[blockIdx.x];
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    int64_t idx = base + (int64_t)threadIdx.x * SCAN_ITEMS + i;
+    if (idx < n) out[idx] = v[i] + off;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = off + total;
+}
+
+// Exclusive scan with total: out[0..n] (n+1 entries). Uses a temporary of ceil(n/TILE) int64.
+template <typename TIn>
+static fea_status exclusive_scan(const TIn* in, int64_t n, int64_t* out, cudaStream_t s) {
+  int64_t tiles = std::max<int64_t>(1, (n + SCAN_TILE - 1) / SCAN_TILE);
+  int64_t* sums = nullptr;
+  FEA_CUDA_TRY(cudaMallocAsync(&sums, sizeof(int64_t) * tiles, s));
+  k_tile_sums<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums);
+  k_scan_tile_sums<<<1, SCAN_THREADS, 0, s>>>(sums, tiles);
+  k_scan_apply<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums, out);
+  cudaError_t e = cudaGetLastError();
+  cudaFreeAsync(sums, s);
+  if (e != cudaSuccess) return fail(FEA_ERR_CUDA, "scan launch: %s", cudaGetErrorString(e));
+  return FEA_OK;
+}
+
+// ------------------------------------------------------------------ mesh validation
+
+template <int TYPE>
+__global__ void k_validate(const double* __restrict__ coords, const int32_t* __restrict__ conn, int64_t n_node,
+                           int64_t n_elem, uint32_t* status) {
+  constexpr int NEN = Elem<TYPE>::NEN, NG = Elem<TYPE>::NG;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_elem) return;
+  const int32_t* ce = conn + e * NEN;
+  int32_t ids[NEN];
+  bool ok = true;
+  for (int a = 0; a < NEN; ++a) {
+    ids[a] = ce[a];
+    if (ids[a] < 0 || ids[a] >= n_node) ok = false;
+  }
+  if (!ok) { atomicOr(status, ST_RANGE); return; }
+  for (int a = 0; a < NEN; ++a)
+    for (int b = a + 1; b < NEN; ++b)
+      if (ids[a] == ids[b]) ok = false;
+  if (!ok) { atomicOr(status, ST_DUP); return; }
+  double x0[3];
+  for (int i = 0; i < 3; ++i) x0[i] = coords[(int64_t)ids[0] * 3 + i];
+  for (int p = 0; p < NG + n_corners<TYPE>(); ++p) {
+    double xi[3], w;
+    if (p < NG) gauss_point<TYPE>(p, xi, w);
+    else corner_point<TYPE>(p - NG, xi);
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int a = 0; a < NEN; ++a) {
+      double N, dN[3];
+      shape<TYPE>(a, xi, N, dN);
+      for (int i = 0; i < 3; ++i) {
+        double xa = coords[(int64_t)ids[a] * 3 + i] - x0[i];
+        for (int j = 0; j < 3; ++j) J[i][j] += xa * dN[j];
+      }
+    }
+    if (!(det3(J) > 0.0)) { atomicOr(status, ST_INVERTED); return; }
+  }
+}
+
+// hi/lo float split of every coordinate, SoA.
+__global__ void k_split_coords(const double* __restrict__ coords, int64_t n_node, float* xhi, float* xlo) {
+  int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_node) return;
+  for (int i = 0; i < 3; ++i) {
+    double x = coords[n * 3 + i];
+    float hi = (float)x;
+    xhi[(int64_t)i * n_node + n] = hi;
+    xlo[(int64_t)i * n_node + n] = (float)(x - (double)hi);
+  }
+}
+
+// ------------------------------------------------------------------ pattern kernels
+
+__global__ void k_inc_count(const int32_t* __restrict__ conn, int64_t total, int32_t* cnt) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < total) atomicAdd(&cnt[conn[t]], 1);
+}
+
+__global__ void k_inc_fill(const int32_t* __restrict__ conn, int64_t total, int nen, const int64_t* inc_ptr,
+                           int32_t* cursor, int32_t* inc_elem) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  int32_t n = conn[t];
+  int32_t k = atomicAdd(&cursor[n], 1);
+  inc_elem[inc_ptr[n] + k] = (int32_t)(t / nen);
+}
+
+static constexpr int ROW_WARPS = 4;
+static constexpr int ROW_CAP = 4096;  // candidate columns per row (incident elements x nen)
+
+// Per-warp bitonic sort of n (power of two) ints in shared memory.
+__device__ void warp_bitonic_sort(int32_t* s, int n) {
+  int lane = threadIdx.x & 31;
+  for (int k = 2; k <= n; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < n; i += 32) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          int32_t a = s[i], b = s[ixj];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) { s[i] = b; s[ixj] = a; }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// One warp per row: gather the nodes of every incident element, sort, unique.
+// mode 0 writes the unique count to rowcnt; mode 1 writes the columns (and sorts
+// the incidence list of the row so later schedules are deterministic).
+__global__ void __launch_bounds__(ROW_WARPS * 32)
+k_rows(const int32_t* __restrict__ conn, int nen, const int64_t* __restrict__ inc_ptr, int32_t* inc_elem,
+       int64_t n_node, int mode, int32_t* rowcnt, const int64_t* __restrict__ rowptr, int32_t* colind,
+       uint32_t* status) {
+  extern __shared__ int32_t sm_rows[];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t* s = sm_rows + w * ROW_CAP;
+  int64_t warps_total = (int64_t)gridDim.x * ROW_WARPS;
+  for (int64_t r = (int64_t)blockIdx.x * ROW_WARPS + w; r < n_node; r += warps_total) {
+    int64_t i0 = inc_ptr[r], i1 = inc_ptr[r + 1];
+    int64_t cnt = (i1 - i0) * nen;
+    if (cnt > ROW_CAP) {
+      if (lane == 0) atomicOr(status, ST_ROW_TOO_LONG);
+      continue;
+    }
+    int n2 = 1;
+    while (n2 < cnt) n2 <<= 1;
+    if (n2 < 2) n2 = 2;
+    if (mode == 1) {
+      // sort this row's incidence list (ascending element ids)
+      int m = (int)(i1 - i0), m2 = 2;
+      while (m2 < m) m2 <<= 1;
+      for (int i = lane; i < m2; i += 32) s[i] = i < m ? inc_elem[i0 + i] : INT_MAX;
+      __syncwarp();
+      warp_bitonic_sort(s, m2);
+      for (int i = lane; i < m; i += 32) inc_elem[i0 + i] = s[i];
+      __syncwarp();
+    }
+    for (int i = lane; i < n2; i += 32) {
+      int32_t v = INT_MAX;
+      if (i < cnt) {
+        int64_t t = i0 + i / nen;
+        v = conn[(int64_t)inc_elem[t] * nen + (i % nen)];
+      }
+      s[i] = v;
+    }
+    __syncwarp();
+    warp_bitonic_sort(s, n2);
+    // unique
+    int64_t written = 0;
+    for (int base = 0; base < cnt; base += 32) {
+      int i = base + lane;
+      bool first = i < cnt && (i == 0 || s[i] != s[i - 1]);
+      unsigned m = __ballot_sync(0xffffffffu, first);
+      if (mode == 1 && first) {
+        int off = __popc(m & ((1u << lane) - 1u));
+        colind[rowptr[r] + written + off] = s[i];
+      }
+      written += __popc(m);
+    }
+    if (mode == 0 && lane == 0) rowcnt[r] = (int32_t)written;
+    __syncwarp();
+  }
+}
+
+__global__ void k_posmap(const int32_t* __restrict__ conn, int64_t n_elem, int nen, const int64_t* __restrict__ rowptr,
+                         const int32_t* __restrict__ colind, int32_t* pos) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t total = n_elem * nen * nen;
+  if (t >= total) return;
+  int64_t e = t / (nen * nen);
+  int ab = (int)(t % (nen * nen));
+  int a = ab / nen, b = ab % nen;
+  int32_t r = conn[e * nen + a], c = conn[e * nen + b];
+  int64_t lo = rowptr[r], hi = rowptr[r + 1] - 1;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (colind[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  pos[t] = (int32_t)lo;
+}
+
+static unsigned grid_for(int64_t n, int threads) { return (unsigned)std::max<int64_t>(1, (n + threads - 1) / threads); }
+
+}  // namespace fea
+
+using namespace fea;
+
+// ------------------------------------------------------------------ C ABI helpers
+
+static fea_status check_assemble_args(fea_mesh* m, const fea_pattern* p, const void* vel, const void* kd,
+                                      const void* sr, const void* phi, double dt, int32_t n_eq,
+                                      const fea_assemble_opts* o, const void* values, const void* rhs) {
+  if (!m || !p) return fail(FEA_ERR_ARG, "mesh/pattern is null");
+  if (p->mesh != m) return fail(FEA_ERR_STATE, "pattern was built for another mesh");
+  if (n_eq <= 0) return fail(FEA_ERR_ARG, "n_eq must be > 0 (got %d)", n_eq);
+  if (!(dt > 0.0)) return fail(FEA_ERR_ARG, "dt must be > 0");
+  if (!vel || !kd || !sr || !phi || !values || !rhs) return fail(FEA_ERR_ARG, "a field or output pointer is null");
+  if (o->precision != FEA_F64_PLAIN && o->precision != FEA_F32_FUSED) return fail(FEA_ERR_ARG, "unknown precision");
+  if (o->terms & ~FEA_TERM_ALL) return fail(FEA_ERR_ARG, "unknown term bits");
+  if (o->scatter < FEA_SCATTER_AUTO || o->scatter > FEA_SCATTER_ROWOWNED) return fail(FEA_ERR_ARG, "unknown scatter");
+  return FEA_OK;
+}
+
+template <typename T>
+static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, const void* kd, const void* sr,
+                            const void* phi, double dt, int32_t n_eq, const fea_assemble_opts* o, void* values,
+                            void* rhs) {
+  AsmArgs<T> a;
+  a.conn = m->conn;
+  a.coords = m->coords;
+  a.xhi = m->xhi;
+  a.xlo = m->xlo;
+  a.pos = p->pos;
+  a.rowptr = p->rowptr;
+  a.colind = p->colind;
+  a.vel = (const T*)vel;
+  a.kd = (const T*)kd;
+  a.sr = (const T*)sr;
+  a.phi = (const T*)phi;
+  a.values = (T*)values;
+  a.rhs = (T*)rhs;
+  a.n_node = m->n_node;
+  a.n_elem = m->n_elem;
+  a.nnz = p->nnz;
+  a.n_eq = n_eq;
+  a.eq0 = 0;
+  a.eq_count = n_eq;
+  a.terms = o->terms;
+  a.dt = dt;
+  a.kappa_threshold = o->kappa_threshold;
+  a.status = m->status;
+  return a;
+}
+
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char* fea_last_error(void) { return g_last_error.c_str(); }
+int32_t fea_version(void) { return 10000; }
+int64_t fea_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+fea_status fea_default_opts(fea_assemble_opts* o) {
+  if (!o) return fail(FEA_ERR_ARG, "opts is null");
+  memset(o, 0, sizeof *o);
+  o->precision = FEA_F32_FUSED;
+  o->terms = FEA_TERM_ALL;
+  o->scatter = FEA_SCATTER_AUTO;
+  o->accumulate = 0;
+  o->kappa_threshold = 1e3;
+  return FEA_OK;
+}
+
+fea_status fea_pack_plan(const int64_t* count_by_type, int32_t n_types, int32_t vector_size, int64_t* packs,
+                         int64_t* pads) {
+  if (!count_by_type || !packs || !pads || n_types < 0 || vector_size <= 0)
+    return fail(FEA_ERR_ARG, "fea_pack_plan: bad argument");
+  for (int t = 0; t < n_types; ++t) {
+    if (count_by_type[t] < 0) return fail(FEA_ERR_ARG, "fea_pack_plan: negative count");
+    packs[t] = (count_by_type[t] + vector_size - 1) / vector_size;
+    pads[t] = packs[t] * vector_size - count_by_type[t];
+  }
+  return FEA_OK;
+}
+
+}  // extern "C"
+static int nen_of(fea_elem_t t) { return t == FEA_TET4 ? 4 : t == FEA_HEX8 ? 8 : t == FEA_HEX27 ? 27 : 0; }
+
+extern "C" {
+fea_status fea_mesh_destroy(fea_mesh* m) {
+  if (!m) return FEA_OK;
+  cudaFree(m->coords);
+  cudaFree(m->xhi);
+  cudaFree(m->xlo);
+  cudaFree(m->conn);
+  cudaFree(m->status);
+  delete m;
+  return FEA_OK;
+}
+
+fea_status fea_mesh_set_stream(fea_mesh* m, void* stream) {
+  if (!m) return fail(FEA_ERR_ARG, "mesh is null");
+  m->stream = (cudaStream_t)stream;
+  return FEA_OK;
+}
+
+fea_status fea_sync(fea_mesh* m) {
+  if (!m) return fail(FEA_ERR_ARG, "mesh is null");
+  FEA_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  uint32_t bits = 0;
+  FEA_CUDA_TRY(cudaMemcpy(&bits, m->status, sizeof bits, cudaMemcpyDeviceToHost));
+  return status_to_error(bits);
+}
+
+fea_status fea_mesh_create(const double* coords, int64_t n_node, const int32_t* conn, int64_t n_elem, fea_elem_t type,
+                           void* stream, fea_mesh** out) {
+  if (!out) return fail(FEA_ERR_ARG, "out is null");
+  *out = nullptr;
+  int nen = nen_of(type);
+  if (!nen) return fail(FEA_ERR_ARG, "unknown element type %d", (int)type);
+  if (n_node <= 0 || n_elem < 0) return fail(FEA_ERR_ARG, "n_node must be > 0 and n_elem >= 0");
+  if (!coords || (n_elem > 0 && !conn)) return fail(FEA_ERR_ARG, "coords/conn is null");
+  if (n_node >= INT32_MAX) return fail(FEA_ERR_TOO_LARGE, "n_node %lld exceeds int32 ids", (long long)n_node);
+  if (n_elem > (int64_t)INT32_MAX / (nen * nen))
+    return fail(FEA_ERR_TOO_LARGE, "n_elem %lld too large for int32 position-map indexing", (long long)n_elem);
+  fea_mesh* m = new (std::nothrow) fea_mesh();
+  if (!m) return fail(FEA_ERR_OOM, "host allocation failed");
+  m->type = type;
+  m->nen = nen;
+  m->n_node = n_node;
+  m->n_elem = n_elem;
+  m->stream = (cudaStream_t)stream;
+  cudaGetDevice(&m->device);
+  cudaStream_t s = m->stream;
+  auto cleanup = [&](fea_status st) { fea_mesh_destroy(m); return st; };
+  size_t cb = sizeof(double) * 3 * n_node, eb = sizeof(int32_t) * nen * std::max<int64_t>(n_elem, 1);
+  if (cudaMalloc(&m->coords, cb) != cudaSuccess || cudaMalloc(&m->xhi, sizeof(float) * 3 * n_node) != cudaSuccess ||
+      cudaMalloc(&m->xlo, sizeof(float) * 3 * n_node) != cudaSuccess || cudaMalloc(&m->conn, eb) != cudaSuccess ||
+      cudaMalloc(&m->status, sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(FEA_ERR_OOM, "device allocation of the mesh failed"));
+  }
+  cudaMemcpyKind kc = is_device_ptr(coords) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpyAsync(m->coords, coords, cb, kc, s) != cudaSuccess) return cleanup(fail(FEA_ERR_CUDA, "coords copy failed"));
+  if (n_elem > 0) {
+    cudaMemcpyKind ke = is_device_ptr(conn) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (cudaMemcpyAsync(m->conn, conn, sizeof(int32_t) * nen * n_elem, ke, s) != cudaSuccess)
+      return cleanup(fail(FEA_ERR_CUDA, "conn copy failed"));
+  }
+  cudaMemsetAsync(m->status, 0, sizeof(uint32_t), s);
+  k_split_coords<<<grid_for(n_node, 256), 256, 0, s>>>(m->coords, n_node, m->xhi, m->xlo);
+  if (n_elem > 0) {
+    unsigned g = grid_for(n_elem, 128);
+    if (type == FEA_TET4) k_validate<FEA_TET4><<<g, 128, 0, s>>>(m->coords, m->conn, n_node, n_elem, m->status);
+    else if (type == FEA_HEX8) k_validate<FEA_HEX8><<<g, 128, 0, s>>>(m->coords, m->conn, n_node, n_elem, m->status);
+    else k_validate<FEA_HEX27><<<g, 128, 0, s>>>(m->coords, m->conn, n_node, n_elem, m->status);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cleanup(fail(FEA_ERR_CUDA, "validation launch: %s", cudaGetErrorString(e)));
+  fea_status st = fea_sync(m);
+  if (st != FEA_OK) return cleanup(st);
+  *out = m;
+  return FEA_OK;
+}
+
+fea_status fea_pattern_destroy(fea_pattern* p) {
+  if (!p) return FEA_OK;
+  cudaFree(p->rowptr);
+  cudaFree(p->colind);
+  cudaFree(p->pos);
+  cudaFree(p->inc_ptr);
+  cudaFree(p->inc_elem);
+  cudaFree(p->ws);
+  plan_destroy(p->plan);
+  delete p;
+  return FEA_OK;
+}
+
+fea_status fea_pattern_get(const fea_pattern* p, const int64_t** rowptr, const int32_t** colind, const int32_t** pos,
+                           int64_t* nnz) {
+  if (!p) return fail(FEA_ERR_ARG, "pattern is null");
+  if (rowptr) *rowptr = p->rowptr;
+  if (colind) *colind = p->colind;
+  if (pos) *pos = p->pos;
+  if (nnz) *nnz = p->nnz;
+  return FEA_OK;
+}
+
+fea_status fea_pattern_build(fea_mesh* m, fea_pattern** out) {
+  if (!m || !out) return fail(FEA_ERR_ARG, "mesh/out is null");
+  *out = nullptr;
+  fea_pattern* p = new (std::nothrow) fea_pattern();
+  if (!p) return fail(FEA_ERR_OOM, "host allocation failed");
+  p->mesh = m;
+  cudaStream_t s = m->stream;
+  auto cleanup = [&](fea_status st) { fea_pattern_destroy(p); return st; };
+  int64_t N = m->n_node, E = m->n_elem;
+  int nen = m->nen;
+  int64_t tot = E * nen;
+  int32_t *cnt = nullptr, *rowcnt = nullptr;
+  if (cudaMalloc(&p->inc_ptr, sizeof(int64_t) * (N + 1)) != cudaSuccess ||
+      cudaMalloc(&p->inc_elem, sizeof(int32_t) * std::max<int64_t>(tot, 1)) != cudaSuccess ||
+      cudaMalloc(&p->rowptr, sizeof(int64_t) * (N + 1)) != cudaSuccess ||
+      cudaMalloc(&cnt, sizeof(int32_t) * N) != cudaSuccess || cudaMalloc(&rowcnt, sizeof(int32_t) * N) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(cnt);
+    cudaFree(rowcnt);
+    return cleanup(fail(FEA_ERR_OOM, "device allocation of the pattern failed"));
+  }
+  auto done = [&](fea_status st) { cudaFree(cnt); cudaFree(rowcnt); return st == FEA_OK ? st : cleanup(st); };
+  cudaMemsetAsync(cnt, 0, sizeof(int32_t) * N, s);
+  cudaMemsetAsync(m->status, 0, sizeof(uint32_t), s);
+  if (tot > 0) k_inc_count<<<grid_for(tot, 256), 256, 0, s>>>(m->conn, tot, cnt);
+  fea_status st = exclusive_scan(cnt, N, p->inc_ptr, s);
+  if (st != FEA_OK) return done(st);
+  cudaMemsetAsync(cnt, 0, sizeof(int32_t) * N, s);
+  if (tot > 0) k_inc_fill<<<grid_for(tot, 256), 256, 0, s>>>(m->conn, tot, nen, p->inc_ptr, cnt, p->inc_elem);
+  size_t smem = sizeof(int32_t) * ROW_CAP * ROW_WARPS;
+  cudaFuncSetAttribute(k_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  unsigned rg = (unsigned)std::min<int64_t>(grid_for(N, ROW_WARPS), 152 * 16);
+  k_rows<<<rg, ROW_WARPS * 32, smem, s>>>(m->conn, nen, p->inc_ptr, p->inc_elem, N, 0, rowcnt, nullptr, nullptr,
+                                          m->status);
+  st = exclusive_scan(rowcnt, N, p->rowptr, s);
+  if (st != FEA_OK) return done(st);
+  int64_t nnz = 0;
+  if (cudaMemcpyAsync(&nnz, p->rowptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return done(fail(FEA_ERR_CUDA, "nnz readback failed"));
+  st = fea_sync(m);
+  if (st != FEA_OK) return done(st);
+  if (nnz >= (int64_t)INT32_MAX) return done(fail(FEA_ERR_TOO_LARGE, "nnz %lld >= 2^31", (long long)nnz));
+  p->nnz = nnz;
+  if (cudaMalloc(&p->colind, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
+      cudaMalloc(&p->pos, sizeof(int32_t) * std::max<int64_t>(tot * nen, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return done(fail(FEA_ERR_OOM, "device allocation of colind/pos failed"));
+  }
+  k_rows<<<rg, ROW_WARPS * 32, smem, s>>>(m->conn, nen, p->inc_ptr, p->inc_elem, N, 1, nullptr, p->rowptr, p->colind,
+                                          m->status);
+  if (tot > 0) k_posmap<<<grid_for(tot * nen, 256), 256, 0, s>>>(m->conn, E, nen, p->rowptr, p->colind, p->pos);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return done(fail(FEA_ERR_CUDA, "pattern launch: %s", cudaGetErrorString(e)));
+  st = fea_sync(m);
+  if (st != FEA_OK) return done(st);
+  st = plan_build(m, p, &p->plan);
+  if (st != FEA_OK) return done(st);
+  *out = p;
+  return done(FEA_OK);
+}
+
+fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, const void* kd, const void* sr,
+                        const void* phi, double dt, int32_t n_eq, const fea_assemble_opts* opts, void* values,
+                        void* rhs) {
+  fea_assemble_opts o;
+  if (opts) o = *opts;
+  else fea_default_opts(&o);
+  FEA_TRY(check_assemble_args(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs));
+  cudaStream_t s = m->stream;
+  size_t es = o.precision == FEA_F64_PLAIN ? sizeof(double) : sizeof(float);
+  bool rowowned = false;
+  if (o.precision == FEA_F32_FUSED && o.scatter != FEA_SCATTER_ATOMIC)
+    rowowned = plan_supports(p->plan, n_eq, o.accumulate);
+  if (o.scatter == FEA_SCATTER_ROWOWNED && !rowowned)
+    return fail(FEA_ERR_ARG, "row-owned scatter is not available for this mesh/precision/accumulate setting");
+  if (!o.accumulate && !rowowned) {
+    FEA_CUDA_TRY(cudaMemsetAsync(values, 0, es * (size_t)n_eq * (size_t)p->nnz, s));
+    FEA_CUDA_TRY(cudaMemsetAsync(rhs, 0, es * (size_t)n_eq * (size_t)m->n_node, s));
+  }
+  if (o.event_begin) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_begin, s));
+  if (m->n_elem > 0) {
+    if (o.precision == FEA_F64_PLAIN) {
+      AsmArgs<double> a = make_args<double>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
+      for (int q = 0; q < n_eq; ++q) {  // one launch per equation, geometry recomputed each time
+        a.eq0 = q;
+        a.eq_count = 1;
+        FEA_TRY(launch_generic_f64(a, m->type, s));
+      }
+    } else {
+      AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
+      if (rowowned) FEA_TRY(plan_assemble(p->plan, a, s));
+      else FEA_TRY(launch_generic_f32(a, m->type, s));
+    }
+  }
+  if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, s));
+  return FEA_OK;
+}
+
+fea_status fea_assemble_host(fea_mesh* m, const fea_pattern* cp, const void* vel, const void* kd, const void* sr,
+                             const void* phi, double dt, int32_t n_eq, const fea_assemble_opts* opts, void* values,
+                             void* rhs) {
+  fea_assemble_opts o;
+  if (opts) o = *opts;
+  else fea_default_opts(&o);
+  FEA_TRY(check_assemble_args(m, cp, vel, kd, sr, phi, dt, n_eq, &o, values, rhs));
+  fea_pattern* p = const_cast<fea_pattern*>(cp);
+  cudaStream_t s = m->stream;
+  size_t es = o.precision == FEA_F64_PLAIN ? sizeof(double) : sizeof(float);
+  size_t N = (size_t)m->n_node, Q = (size_t)n_eq, nnz = (size_t)p->nnz;
+  size_t b_vel = es * 3 * N, b_f = es * Q * N, b_val = es * Q * nnz;
+  size_t need = b_vel + 3 * b_f + b_val + b_f + 8 * 256;
+  if (p->ws_bytes < need) {
+    cudaFree(p->ws);
+    p->ws = nullptr;
+    p->ws_bytes = 0;
+    FEA_CUDA_TRY(cudaMalloc(&p->ws, need));
+    p->ws_bytes = need;
+  }
+  auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  char* base = (char*)p->ws;
+  char* d_vel = base;
+  char* d_kd = d_vel + al(b_vel);
+  char* d_sr = d_kd + al(b_f);
+  char* d_phi = d_sr + al(b_f);
+  char* d_val = d_phi + al(b_f);
+  char* d_rhs = d_val + al(b_val);
+  FEA_CUDA_TRY(cudaMemcpyAsync(d_vel, vel, b_vel, cudaMemcpyHostToDevice, s));
+  FEA_CUDA_TRY(cudaMemcpyAsync(d_kd, kd, b_f, cudaMemcpyHostToDevice, s));
+  FEA_CUDA_TRY(cudaMemcpyAsync(d_sr, sr, b_f, cudaMemcpyHostToDevice, s));
+  FEA_CUDA_TRY(cudaMemcpyAsync(d_phi, phi, b_f, cudaMemcpyHostToDevice, s));
+  if (o.accumulate) {
+    FEA_CUDA_TRY(cudaMemcpyAsync(d_val, values, b_val, cudaMemcpyHostToDevice, s));
+    FEA_CUDA_TRY(cudaMemcpyAsync(d_rhs, rhs, b_f, cudaMemcpyHostToDevice, s));
+  }
+  FEA_TRY(fea_assemble(m, p, d_vel, d_kd, d_sr, d_phi, dt, n_eq, &o, d_val, d_rhs));
+  FEA_CUDA_TRY(cudaMemcpyAsync(values, d_val, b_val, cudaMemcpyDeviceToHost, s));
+  FEA_CUDA_TRY(cudaMemcpyAsync(rhs, d_rhs, b_f, cudaMemcpyDeviceToHost, s));
+  return fea_sync(m);
+}
+
+}  // extern "C"

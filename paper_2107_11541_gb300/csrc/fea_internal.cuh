@@ -1,0 +1,230 @@
+// fea_internal.cuh -- shared internals of the CUDA assembly library: handle
+// structs, error plumbing and the reference elements (shape functions and
+// Gauss rules) as the device code evaluates them.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "fea.h"
+
+namespace fea {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const char* fmt, ...);
+fea_status fail(fea_status st, const char* fmt, ...);
+// Adds n to the process-wide count of kernels this library launched.
+void count_launches(int64_t n);
+
+#define FEA_CUDA_TRY(call)                                                                       \
+  do {                                                                                           \
+    cudaError_t e__ = (call);                                                                    \
+    if (e__ != cudaSuccess) {                                                                    \
+      return ::fea::fail(e__ == cudaErrorMemoryAllocation ? FEA_ERR_OOM : FEA_ERR_CUDA,          \
+                         "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e__), __FILE__,      \
+                         __LINE__);                                                              \
+    }                                                                                            \
+  } while (0)
+
+#define FEA_TRY(call)                         \
+  do {                                        \
+    fea_status s__ = (call);                  \
+    if (s__ != FEA_OK) return s__;            \
+  } while (0)
+
+// Device status word bits (written by kernels, never trapped on).
+enum : uint32_t {
+  ST_RANGE = 1u,
+  ST_DUP = 2u,
+  ST_INVERTED = 4u,
+  ST_ROW_TOO_LONG = 8u,
+  ST_TIMEOUT = 16u,
+  ST_SCHEDULE = 32u,
+};
+fea_status status_to_error(uint32_t bits);
+
+// ------------------------------------------------------------------ handles
+
+}  // namespace fea
+
+struct fea_mesh {
+  fea_elem_t type;
+  int nen;
+  int64_t n_node;
+  int64_t n_elem;
+  cudaStream_t stream;
+  int device;
+  double* coords;     // [n_node][3] FP64
+  float* xhi;         // [3][n_node] high part of each coordinate (float)
+  float* xlo;         // [3][n_node] low part: coordinate - hi, rounded to float
+  int32_t* conn;      // [n_elem][nen]
+  uint32_t* status;   // device status word
+};
+
+struct fea_rowowned_plan;  // schedules of the row-owned kernels (per element type)
+
+struct fea_pattern {
+  fea_mesh* mesh;
+  int64_t nnz;
+  int64_t* rowptr;     // [n_node+1]
+  int32_t* colind;     // [nnz]
+  int32_t* pos;        // [n_elem][nen][nen]
+  int64_t* inc_ptr;    // [n_node+1] node -> element incidence
+  int32_t* inc_elem;   // [nen*n_elem]
+  fea_rowowned_plan* plan;  // may be null (row-owned path unavailable for this mesh)
+  // device workspace for fea_assemble_host
+  void* ws;
+  size_t ws_bytes;
+};
+
+namespace fea {
+
+// ------------------------------------------------------------------ reference elements
+//
+// Tet4: N = (1-xi-eta-zeta, xi, eta, zeta); 4-point rule whose point g has
+//   barycentric weight alpha on vertex g and beta on the others,
+//   alpha = (5+3 sqrt5)/20, beta = (5-sqrt5)/20, weight 1/24 (degree 2 exact).
+// Hex8:  trilinear, node a = i+2j+4k <-> (xi,eta,zeta) = (+-1,+-1,+-1);
+//   2x2x2 Gauss-Legendre, points +-1/sqrt3, weight 1.
+// Hex27: triquadratic, node a = i+3j+9k <-> {-1,0,1}^3;
+//   3x3x3 Gauss-Legendre, points 0, +-sqrt(3/5), weights 8/9, 5/9.
+// Gauss points are numbered like the nodes (x fastest).
+
+template <int TYPE> struct Elem;
+template <> struct Elem<FEA_TET4> { static constexpr int NEN = 4, NG = 4, ORDER = 1; };
+template <> struct Elem<FEA_HEX8> { static constexpr int NEN = 8, NG = 8, ORDER = 1; };
+template <> struct Elem<FEA_HEX27> { static constexpr int NEN = 27, NG = 27, ORDER = 2; };
+
+// 1-D Lagrange basis on [-1,1]: value and derivative of function i at t.
+template <int ORDER, typename T>
+__host__ __device__ inline void basis1d(int i, T t, T& v, T& d) {
+  if (ORDER == 1) {
+    v = i == 0 ? (T(1) - t) * T(0.5) : (T(1) + t) * T(0.5);
+    d = i == 0 ? T(-0.5) : T(0.5);
+  } else {
+    if (i == 0) { v = T(0.5) * t * (t - T(1)); d = t - T(0.5); }
+    else if (i == 1) { v = T(1) - t * t; d = T(-2) * t; }
+    else { v = T(0.5) * t * (t + T(1)); d = t + T(0.5); }
+  }
+}
+
+// Reference coordinates and weight of Gauss point g.
+template <int TYPE>
+__host__ __device__ inline void gauss_point(int g, double xi[3], double& w) {
+  if (TYPE == FEA_TET4) {
+    const double alpha = 0.58541019662496845446;  // (5 + 3 sqrt 5) / 20
+    const double beta = 0.13819660112501051518;   // (5 - sqrt 5) / 20
+    xi[0] = g == 1 ? alpha : beta;
+    xi[1] = g == 2 ? alpha : beta;
+    xi[2] = g == 3 ? alpha : beta;
+    w = 1.0 / 24.0;
+  } else if (TYPE == FEA_HEX8) {
+    const double p = 0.57735026918962576451;  // 1 / sqrt 3
+    xi[0] = (g & 1) ? p : -p;
+    xi[1] = (g & 2) ? p : -p;
+    xi[2] = (g & 4) ? p : -p;
+    w = 1.0;
+  } else {
+    const double p = 0.77459666924148337704;  // sqrt(3/5)
+    const double pt[3] = {-p, 0.0, p};
+    const double wt[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    int i = g % 3, j = (g / 3) % 3, k = g / 9;
+    xi[0] = pt[i];
+    xi[1] = pt[j];
+    xi[2] = pt[k];
+    w = wt[i] * wt[j] * wt[k];
+  }
+}
+
+// Shape function a and its reference gradient at xi.
+template <int TYPE, typename T>
+__host__ __device__ inline void shape(int a, const T xi[3], T& N, T dN[3]) {
+  if (TYPE == FEA_TET4) {
+    if (a == 0) { N = T(1) - xi[0] - xi[1] - xi[2]; dN[0] = dN[1] = dN[2] = T(-1); }
+    else { N = xi[a - 1]; dN[0] = a == 1; dN[1] = a == 2; dN[2] = a == 3; }
+  } else {
+    constexpr int ORDER = Elem<TYPE>::ORDER, Q = ORDER + 1;
+    int i = a % Q, j = (a / Q) % Q, k = a / (Q * Q);
+    T lx, dx, ly, dy, lz, dz;
+    basis1d<ORDER>(i, xi[0], lx, dx);
+    basis1d<ORDER>(j, xi[1], ly, dy);
+    basis1d<ORDER>(k, xi[2], lz, dz);
+    N = lx * ly * lz;
+    dN[0] = dx * ly * lz;
+    dN[1] = lx * dy * lz;
+    dN[2] = lx * ly * dz;
+  }
+}
+
+// Corner points used by the orientation check (Tet4 vertices, hex corners).
+template <int TYPE>
+__host__ __device__ inline void corner_point(int c, double xi[3]) {
+  if (TYPE == FEA_TET4) {
+    xi[0] = c == 1; xi[1] = c == 2; xi[2] = c == 3;
+  } else {
+    xi[0] = (c & 1) ? 1.0 : -1.0;
+    xi[1] = (c & 2) ? 1.0 : -1.0;
+    xi[2] = (c & 4) ? 1.0 : -1.0;
+  }
+}
+template <int TYPE> constexpr int n_corners() { return TYPE == FEA_TET4 ? 4 : 8; }
+
+template <typename T>
+__host__ __device__ inline T det3(const T J[3][3]) {
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+// Inverse transpose scaled by 1/det: returns G with G[i][j] = (J^-1)[j][i].
+template <typename T>
+__host__ __device__ inline void inv_transpose3(const T J[3][3], T det, T G[3][3]) {
+  T r = T(1) / det;
+  G[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) * r;
+  G[1][0] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * r;
+  G[2][0] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * r;
+  G[0][1] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) * r;
+  G[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * r;
+  G[2][1] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * r;
+  G[0][2] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) * r;
+  G[1][2] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * r;
+  G[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * r;
+}
+
+// Parameters shared by the assembly kernels.
+template <typename T>
+struct AsmArgs {
+  const int32_t* conn;
+  const double* coords;  // [N][3]
+  const float* xhi;      // [3][N]
+  const float* xlo;      // [3][N]
+  const int32_t* pos;
+  const int64_t* rowptr;
+  const int32_t* colind;
+  const T* vel;    // [3][N]
+  const T* kd;     // [n_eq][N]
+  const T* sr;     // [n_eq][N]
+  const T* phi;    // [n_eq][N]
+  T* values;       // [n_eq][nnz]
+  T* rhs;          // [n_eq][N]
+  int64_t n_node;
+  int64_t n_elem;
+  int64_t nnz;
+  int n_eq;        // total equations (array strides)
+  int eq0;         // first equation handled by this launch
+  int eq_count;    // equations handled by this launch
+  int terms;
+  double dt;
+  double kappa_threshold;
+  uint32_t* status;
+};
+
+// Launchers (defined in the kernel translation units).
+fea_status launch_generic_f64(const AsmArgs<double>& a, fea_elem_t type, cudaStream_t s);
+fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s);
+
+}  // namespace fea

@@ -1,0 +1,204 @@
+"""ctypes binding of the C ABI in ``include/fea.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls.  Device arrays
+are torch CUDA tensors (PyTorch supplies device memory and streams); all the
+arithmetic runs in the CUDA library ``_build/libfea.so``.  If that library is
+missing the import of any call raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libfea.so")
+
+FEA_TET4, FEA_HEX8, FEA_HEX27 = 0, 1, 2
+FEA_F64_PLAIN, FEA_F32_FUSED = 0, 1
+FEA_TERM_MASS, FEA_TERM_CONV, FEA_TERM_DIFF, FEA_TERM_REAC, FEA_TERM_SUPG, FEA_TERM_ALL = 1, 2, 4, 8, 16, 31
+FEA_SCATTER_AUTO, FEA_SCATTER_ATOMIC, FEA_SCATTER_ROWOWNED = 0, 1, 2
+STATUS = {0: "FEA_OK", 1: "FEA_ERR_ARG", 2: "FEA_ERR_RANGE", 3: "FEA_ERR_DUP_NODE", 4: "FEA_ERR_INVERTED",
+          5: "FEA_ERR_TOO_LARGE", 6: "FEA_ERR_OOM", 7: "FEA_ERR_CUDA", 8: "FEA_ERR_TIMEOUT", 9: "FEA_ERR_STATE"}
+NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27}
+
+# Every symbol include/fea.h declares (checked by the tests).
+EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_destroy", "fea_mesh_set_stream", "fea_sync",
+           "fea_pattern_build", "fea_pattern_get", "fea_pattern_destroy", "fea_assemble", "fea_assemble_host",
+           "fea_pack_plan", "fea_last_error", "fea_kernel_launches", "fea_version"]
+
+
+class FeaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = STATUS.get(code, str(code))
+
+
+class fea_assemble_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("terms", C.c_int32), ("scatter", C.c_int32), ("accumulate", C.c_int32),
+                ("kappa_threshold", C.c_double), ("event_begin", C.c_void_p), ("event_end", C.c_void_p),
+                ("reserved", C.c_int32 * 4)]
+
+
+_lib = None
+
+
+def lib(path: str = LIB_PATH):
+    """Loads the CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise FileNotFoundError(f"{path} is missing: build it first (python -c 'import __graft_entry__ as g; "
+                                    f"g.build()')")
+        L = C.CDLL(path)
+        vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        L.fea_default_opts.argtypes = [C.POINTER(fea_assemble_opts)]
+        L.fea_mesh_create.argtypes = [vp, i64, vp, i64, C.c_int, vp, C.POINTER(vp)]
+        L.fea_mesh_destroy.argtypes = [vp]
+        L.fea_mesh_set_stream.argtypes = [vp, vp]
+        L.fea_sync.argtypes = [vp]
+        L.fea_pattern_build.argtypes = [vp, C.POINTER(vp)]
+        L.fea_pattern_get.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i64)]
+        L.fea_pattern_destroy.argtypes = [vp]
+        L.fea_assemble.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(fea_assemble_opts), vp, vp]
+        L.fea_assemble_host.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(fea_assemble_opts), vp, vp]
+        L.fea_pack_plan.argtypes = [vp, i32, i32, vp, vp]
+        L.fea_last_error.restype = C.c_char_p
+        L.fea_version.restype = C.c_int32
+        L.fea_kernel_launches.restype = C.c_int64
+        for name in EXPORTS:
+            if name not in ("fea_last_error", "fea_version", "fea_kernel_launches"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != 0:
+        raise FeaError(code, lib().fea_last_error().decode())
+
+
+def _ptr(x) -> int | None:
+    """Address of a torch tensor or numpy array (None passes NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def fea_default_opts(**kw) -> fea_assemble_opts:
+    o = fea_assemble_opts()
+    _check(lib().fea_default_opts(C.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def fea_mesh_create(coords, conn, elem_type: int, stream=None) -> C.c_void_p:
+    """coords [N][3] float64 and conn [E][nen] int32, numpy (host) or torch CUDA tensors."""
+    if isinstance(coords, np.ndarray):
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+        conn = np.ascontiguousarray(conn, dtype=np.int32)
+    else:
+        assert coords.dtype.__str__() == "torch.float64" and conn.dtype.__str__() == "torch.int32"
+        assert coords.is_contiguous() and conn.is_contiguous()
+    out = C.c_void_p()
+    _check(lib().fea_mesh_create(_ptr(coords), coords.shape[0], _ptr(conn), conn.shape[0], int(elem_type),
+                                 _stream_ptr(stream), C.byref(out)))
+    return out
+
+
+def fea_mesh_destroy(mesh):
+    _check(lib().fea_mesh_destroy(mesh))
+
+
+def fea_mesh_set_stream(mesh, stream):
+    _check(lib().fea_mesh_set_stream(mesh, _stream_ptr(stream)))
+
+
+def fea_sync(mesh):
+    _check(lib().fea_sync(mesh))
+
+
+def fea_pattern_build(mesh) -> C.c_void_p:
+    out = C.c_void_p()
+    _check(lib().fea_pattern_build(mesh, C.byref(out)))
+    return out
+
+
+def fea_pattern_get(pattern):
+    """(rowptr, colind, pos, nnz): borrowed device addresses and the nnz."""
+    r, c, p, n = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_int64()
+    _check(lib().fea_pattern_get(pattern, C.byref(r), C.byref(c), C.byref(p), C.byref(n)))
+    return r.value, c.value, p.value, n.value
+
+
+def fea_pattern_destroy(pattern):
+    _check(lib().fea_pattern_destroy(pattern))
+
+
+def fea_assemble(mesh, pattern, velocity, diffusivity, reaction, phi_old, dt: float, n_eq: int, opts, values, rhs):
+    """All arrays are torch CUDA tensors of the precision's dtype; enqueued on the mesh's stream."""
+    _check(lib().fea_assemble(mesh, pattern, _ptr(velocity), _ptr(diffusivity), _ptr(reaction), _ptr(phi_old),
+                              float(dt), int(n_eq), C.byref(opts) if opts is not None else None, _ptr(values),
+                              _ptr(rhs)))
+
+
+def fea_assemble_host(mesh, pattern, velocity, diffusivity, reaction, phi_old, dt: float, n_eq: int, opts, values,
+                      rhs):
+    """Host-array variant (numpy or pinned torch CPU tensors); waits for completion."""
+    _check(lib().fea_assemble_host(mesh, pattern, _ptr(velocity), _ptr(diffusivity), _ptr(reaction), _ptr(phi_old),
+                                   float(dt), int(n_eq), C.byref(opts) if opts is not None else None, _ptr(values),
+                                   _ptr(rhs)))
+
+
+def fea_pack_plan(count_by_type, vector_size: int):
+    counts = np.ascontiguousarray(count_by_type, dtype=np.int64)
+    packs = np.zeros_like(counts)
+    pads = np.zeros_like(counts)
+    _check(lib().fea_pack_plan(counts.ctypes.data, counts.size, int(vector_size), packs.ctypes.data,
+                               pads.ctypes.data))
+    return packs, pads
+
+
+def fea_last_error() -> str:
+    return lib().fea_last_error().decode()
+
+
+def fea_kernel_launches() -> int:
+    return lib().fea_kernel_launches()
+
+
+def fea_version() -> int:
+    return lib().fea_version()
+
+
+# ------------------------------------------------------------------ device-array views
+
+class _DevView:
+    """Exposes a borrowed device buffer through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def pattern_tensors(pattern, n_node: int, n_elem: int, nen: int):
+    """Copies of the pattern arrays as torch CUDA tensors: rowptr, colind, pos."""
+    import torch
+    r, c, p, nnz = fea_pattern_get(pattern)
+    rowptr = torch.as_tensor(_DevView(r, (n_node + 1,), "<i8"), device="cuda").clone()
+    colind = torch.as_tensor(_DevView(c, (max(nnz, 1),), "<i4"), device="cuda")[:nnz].clone()
+    pos = torch.as_tensor(_DevView(p, (max(n_elem, 1), nen, nen), "<i4"), device="cuda")[:n_elem].clone()
+    return rowptr, colind, pos

@@ -1,0 +1,77 @@
+"""Host-side checks that need no GPU: the C-ABI library loads and exports every
+symbol include/fea.h declares, argument errors are reported before any device
+work, the Fig. 3 packing layout, and the synthetic meshes are valid."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2107_11541_gb300 import build, fea
+from paper_2107_11541_gb300 import meshgen as G
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return fea.lib()
+
+
+def header_symbols():
+    text = open(os.path.join(ROOT, "include", "fea.h")).read()
+    return sorted(set(re.findall(r"FEA_API\s+[\w\s\*]+?\b(fea_\w+)\s*\(", text)))
+
+
+def test_exports_match_header(L):
+    syms = header_symbols()
+    assert syms == sorted(fea.EXPORTS)
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_version_and_defaults(L):
+    assert fea.fea_version() >= 10000
+    o = fea.fea_default_opts()
+    assert (o.precision, o.terms, o.scatter, o.accumulate, o.kappa_threshold) == (1, 31, 0, 0, 1e3)
+
+
+def test_argument_errors_without_device(L):
+    with pytest.raises(fea.FeaError) as e:
+        fea.lib()
+        fea._check(L.fea_mesh_create(None, 10, None, 0, 1, None, None))
+    assert e.value.code == 1
+    with pytest.raises(fea.FeaError) as e:
+        fea._check(L.fea_mesh_create(None, 10, None, 0, 7, None, None))
+    assert e.value.code == 1
+    with pytest.raises(fea.FeaError) as e:
+        fea.fea_assemble(None, None, None, None, None, None, 1e-3, 1, None, None, None)
+    assert e.value.code == 1
+    assert "null" in fea.fea_last_error()
+
+
+def test_pack_plan_fig3(L):
+    rows = [l.split() for l in open(os.path.join(ROOT, "tests", "golden", "fig3_packing.txt")) if l[0] != "#"]
+    counts = [int(r[1]) for r in rows]
+    vs = int(rows[0][2])
+    packs, pads = fea.fea_pack_plan(counts, vs)
+    assert packs.tolist() == [int(r[3]) for r in rows]
+    assert pads.tolist() == [int(r[4]) for r in rows]
+    with pytest.raises(fea.FeaError):
+        fea.fea_pack_plan([3], 0)
+
+
+@pytest.mark.parametrize("t", (G.TET4, G.HEX8, G.HEX27))
+def test_generated_meshes_are_valid(t):
+    for idx in range(4):
+        w = G.make_workload(idx, n=4 if t != G.HEX27 else 2, n_eq=2)
+        if w.mesh.elem_type != t:
+            continue
+        assert O.validate(t, w.mesh.coords, w.mesh.conn) == O.OK
+    w = G.make_workload(3, n=4, n_eq=1, stretched_slab=True)
+    assert O.validate(G.HEX27, w.mesh.coords, w.mesh.conn) == O.OK
+    w = G.make_workload(1, n=5, n_eq=1)
+    assert O.validate(G.TET4, w.mesh.coords, w.mesh.conn) == O.OK
+    assert sorted(np.unique(w.mesh.conn)) == list(range(w.mesh.n_node))
