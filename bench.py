@@ -139,10 +139,9 @@ def profiled_traffic(workload: str):
         return None
 
 
-def make(workload: str):
-    idx = WORKLOADS[workload]
-    w = G.make_workload(idx)
-    return w
+def make(workload: str, n=None):
+    """The named workload; ``n`` shrinks it to n cells per axis (profiling captures only)."""
+    return G.make_workload(WORKLOADS[workload], n=n)
 
 
 def cpu_oracle_sample(w, budget_s: float):
@@ -214,9 +213,10 @@ def main():
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cells", type=int, default=None, help="shrink to this many cells per axis (profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
-    w = make(args.workload)
+    w = make(args.workload, args.cells)
     if args.impl == "reference":
         run_reference(args, w, rank)
         return

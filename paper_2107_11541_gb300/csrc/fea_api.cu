@@ -588,9 +588,9 @@ fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, cons
   size_t es = o.precision == FEA_F64_PLAIN ? sizeof(double) : sizeof(float);
   bool rowowned = false;
   if (o.precision == FEA_F32_FUSED && o.scatter != FEA_SCATTER_ATOMIC)
-    rowowned = plan_supports(p->plan, n_eq, o.accumulate);
+    FEA_TRY(plan_prepare(p->plan, n_eq, &rowowned));
   if (o.scatter == FEA_SCATTER_ROWOWNED && !rowowned)
-    return fail(FEA_ERR_ARG, "row-owned scatter is not available for this mesh/precision/accumulate setting");
+    return fail(FEA_ERR_ARG, "row-owned scatter is not available for this mesh type, precision or equation count");
   if (!o.accumulate && !rowowned) {
     FEA_CUDA_TRY(cudaMemsetAsync(values, 0, es * (size_t)n_eq * (size_t)p->nnz, s));
     FEA_CUDA_TRY(cudaMemsetAsync(rhs, 0, es * (size_t)n_eq * (size_t)m->n_node, s));
@@ -606,7 +606,7 @@ fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, cons
       }
     } else {
       AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
-      if (rowowned) FEA_TRY(plan_assemble(p->plan, a, s));
+      if (rowowned) FEA_TRY(plan_assemble(p->plan, a, o.accumulate, s));
       else FEA_TRY(launch_generic_f32(a, m->type, s));
     }
   }

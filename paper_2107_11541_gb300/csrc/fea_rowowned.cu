@@ -1,20 +1,503 @@
-// fea_rowowned.cu -- row-owned assembly (placeholder: no schedule yet).
+// fea_rowowned.cu -- row-owned fused FP32 assembly of Hex8 meshes.
+//
+// Every CSR row (node) is owned by exactly one work unit.  A unit is a pencil of
+// nodes (a tile in x-y, a range in z) together with every element incident to
+// its nodes, swept in z order in batches.  Element matrices of all equations
+// are accumulated in shared memory rows and each row is written to HBM once,
+// with plain stores, as soon as its last incident element has been processed:
+// no output zeroing, no global atomics, and the result does not depend on
+// scheduling (bitwise reproducible).  Elements on the boundary of a pencil are
+// computed by each unit that owns one of their nodes (halo recompute).
+//
+// Per element and Gauss point the geometry (Jacobian, det, inverse-transpose,
+// physical gradients, w det J, u.grad N_a, the symmetric products
+// dV grad N_a . grad N_b and |u|) is computed once and shared by all equations
+// through shared memory; per equation a lane forms the Galerkin + SUPG element
+// matrix as a sum over Gauss points of the rank-1 products P_a Q_b
+// (P_a = dV (N_a + tau u.grad N_a), Q_b = (1/dt + s) N_b + u.grad N_b) plus
+// the diffusion sum k_g dV grad N_a . grad N_b (Sec. 4.2, Listing 1,
+// generalised to the full operator).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <vector>
+
 #include "fea_plan.cuh"
 
+namespace fea {
+namespace ro {
+
+constexpr int NEN = 8, NG = 8;
+constexpr int BEMAX = 24;               // elements per batch at most: geometry uses <= 6 warps, >= 2 flush
+constexpr int THREADS = 256;            // 8 warps
+constexpr int LOOKAHEAD = 64;           // sweep positions scanned when colouring a batch
+constexpr int GEO = 48;                 // floats per Gauss point: dv, cu, ua[8], Gd[36], pad[2]
+constexpr int GEO_ELEM = NG * GEO + 4;  // + ck (4/h^2) and padding
+constexpr int OFFS = NEN * NEN + NEN;   // entry offsets per element visit (matrix, then RHS)
+constexpr uint16_t NONE = 0xFFFF;
+constexpr int SMEM_LIMIT = 232448;      // opt-in shared memory per block on sm_103
+
+struct Variant {
+  int n_eq = 0, neqs = 0, n_units = 0, n_slots = 0, row_stride = 0, maxcol = 0, be = 0;
+  int64_t n_visits = 0, n_batches = 0, n_flush = 0;
+  size_t smem = 0;
+  bool unused_nodes = false;
+  int32_t* unit_batch = nullptr;   // [n_units][2] first and end batch, largest unit first
+  int32_t* batch_visit = nullptr;  // [n_batches+1]
+  int32_t* batch_flush = nullptr;  // [n_batches+1]
+  int32_t* visit_nodes = nullptr;  // [n_visits][NEN] node ids of the visited element
+  uint16_t* visit_off = nullptr;   // [n_visits][OFFS]
+  int32_t* flush_row = nullptr;    // [n_flush]
+  int32_t* flush_slot = nullptr;   // [n_flush]
+  float* fnode = nullptr;          // [N][3 n_eq + 3] node-major k, s, phi_old (equation fastest) and u
+  bool ok = false;
+};
+
+// Batch size: one thread per (element, equation), at least one element.
+// Two (element, equation) items per thread when that keeps the threads busy, else one.
+static int batch_elems(int n_eq) {
+  int be2 = std::max(1, std::min(BEMAX, 2 * THREADS / n_eq));
+  if (be2 * n_eq >= (2 * THREADS * 85) / 100) return be2;
+  return std::max(1, std::min(BEMAX, THREADS / n_eq));
+}
+
+// Shared memory besides the row window, for batches of `be` elements.
+// Geometry of a batch plus two staging buffers (raw node data, node ids, offsets).
+static size_t smem_fixed(int be) {
+  return sizeof(float) * (size_t)be * (GEO_ELEM + 2 * (NEN * 9 + NEN + OFFS / 2));
+}
+
+}  // namespace ro
+}  // namespace fea
+
 struct fea_rowowned_plan {
-  int dummy;
+  fea_mesh* mesh = nullptr;
+  fea_pattern* pattern = nullptr;
+  std::mutex mu;
+  std::map<int, fea::ro::Variant*> variants;
+  // host copies, filled on the first prepare
+  bool host_ready = false;
+  std::vector<int32_t> conn;
+  std::vector<double> coords;
+  std::vector<int64_t> rowptr, inc_ptr;
+  std::vector<int32_t> colind, inc_elem;
 };
 
 namespace fea {
+namespace ro {
 
-fea_status plan_build(fea_mesh*, fea_pattern*, fea_rowowned_plan** out) {
-  *out = nullptr;
+// ------------------------------------------------------------------ host schedule
+
+struct Builder {
+  const fea_rowowned_plan& P;
+  int64_t N, E;
+  int n_slots, maxcol, row_stride, be;
+  std::vector<int32_t> owner;      // unit being simulated that owns the node, or -1
+  std::vector<int32_t> slot_of;    // node -> slot during simulation
+  std::vector<int32_t> last_use;   // node -> last element position in the unit
+  std::vector<uint8_t> touched;
+  // outputs
+  std::vector<int32_t> unit_batch{0}, batch_visit{0}, batch_flush{0}, visit_nodes, flush_row, flush_slot;
+  int64_t visits() const { return (int64_t)visit_nodes.size() / NEN; }
+  std::vector<uint16_t> visit_off;
+
+  Builder(const fea_rowowned_plan& p, int slots, int mc, int batch)
+      : P(p), N((int64_t)p.rowptr.size() - 1), E((int64_t)p.conn.size() / NEN), n_slots(slots), maxcol(mc),
+        row_stride(((mc + 1) + 3) & ~3), be(batch), owner(N, -1), slot_of(N, -1), last_use(N, -1), touched(N, 0) {}
+
+  double cz(int32_t e, int d) const {
+    double s = 0;
+    for (int a = 0; a < NEN; ++a) s += P.coords[(int64_t)P.conn[(int64_t)e * NEN + a] * 3 + d];
+    return s / NEN;
+  }
+
+  int colpos(int32_t r, int32_t c) const {
+    const int32_t* b = P.colind.data() + P.rowptr[r];
+    const int32_t* e = P.colind.data() + P.rowptr[r + 1];
+    return (int)(std::lower_bound(b, e, c) - b);
+  }
+
+  // Simulates the sweep of one unit; appends its schedule and returns true, or
+  // returns false (nothing appended) when some batch cannot fit in the slots.
+  bool unit(const std::vector<int32_t>& nodes, int32_t uid) {
+    for (int32_t n : nodes) owner[n] = uid;
+    std::vector<int32_t> els;
+    for (int32_t n : nodes)
+      for (int64_t t = P.inc_ptr[n]; t < P.inc_ptr[n + 1]; ++t) els.push_back(P.inc_elem[t]);
+    std::sort(els.begin(), els.end());
+    els.erase(std::unique(els.begin(), els.end()), els.end());
+    std::vector<std::array<double, 3>> key(els.size());
+    for (size_t i = 0; i < els.size(); ++i) key[i] = {cz(els[i], 2), cz(els[i], 1), cz(els[i], 0)};
+    std::vector<int32_t> order(els.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+      if (key[a] != key[b]) return key[a] < key[b];
+      return els[a] < els[b];
+    });
+    std::vector<int32_t> seq(els.size());
+    for (size_t i = 0; i < els.size(); ++i) seq[i] = els[order[i]];
+    // remaining[n] (kept in last_use): incident elements of owned node n not yet processed
+    for (int32_t e : seq)
+      for (int a = 0; a < NEN; ++a) {
+        int32_t n = P.conn[(int64_t)e * NEN + a];
+        if (owner[n] == uid) last_use[n] = (last_use[n] < 0 ? 0 : last_use[n]) + 1;
+      }
+
+    size_t mark_b = batch_visit.size(), mark_v = (size_t)visits(), mark_f = flush_row.size();
+    std::vector<int32_t> free_slots(n_slots);
+    for (int i = 0; i < n_slots; ++i) free_slots[i] = n_slots - 1 - i;
+    std::vector<uint8_t> done(seq.size(), 0);
+    int live = 0;
+    size_t head = 0;
+    bool ok = true;
+    std::vector<int32_t> fresh, batch, in_batch;
+    while (head < seq.size()) {
+      // Greedy colouring in a look-ahead window of the sweep: the elements of a
+      // batch share no owned node, so the kernel accumulates them without atomics.
+      fresh.clear();
+      batch.clear();
+      int scanned = 0;
+      for (size_t i = head; i < seq.size() && (int)batch.size() < be && scanned < LOOKAHEAD; ++i) {
+        if (done[i]) continue;
+        ++scanned;
+        const int32_t* ce = &P.conn[(int64_t)seq[i] * NEN];
+        bool clash = false;
+        int k = 0;
+        for (int a = 0; a < NEN; ++a) {
+          if (owner[ce[a]] != uid) continue;
+          if (touched[ce[a]] == 2) clash = true;
+          if (!touched[ce[a]]) ++k;
+        }
+        if (clash) continue;
+        if (live + (int)fresh.size() + k > n_slots) break;
+        for (int a = 0; a < NEN; ++a) {
+          if (owner[ce[a]] != uid) continue;
+          if (!touched[ce[a]]) fresh.push_back(ce[a]);
+          touched[ce[a]] = 2;  // 2: in the current batch, 1: live from an earlier batch
+          in_batch.push_back(ce[a]);
+        }
+        done[i] = 1;
+        batch.push_back(seq[i]);
+      }
+      for (int32_t n : in_batch) touched[n] = 1;
+      in_batch.clear();
+      if (batch.empty()) { ok = false; break; }
+      while (head < seq.size() && done[head]) ++head;
+      for (int32_t n : fresh) {
+        slot_of[n] = free_slots.back();
+        free_slots.pop_back();
+      }
+      live += (int)fresh.size();
+      for (int32_t e : batch) {
+        const int32_t* ce = &P.conn[(int64_t)e * NEN];
+        visit_nodes.insert(visit_nodes.end(), ce, ce + NEN);
+        uint16_t off[OFFS];
+        for (int a = 0; a < NEN; ++a) {
+          bool own = owner[ce[a]] == uid;
+          int base = own ? slot_of[ce[a]] * row_stride : 0;
+          for (int b = 0; b < NEN; ++b) off[a * NEN + b] = own ? (uint16_t)(base + colpos(ce[a], ce[b])) : NONE;
+          off[NEN * NEN + a] = own ? (uint16_t)(base + maxcol) : NONE;
+        }
+        visit_off.insert(visit_off.end(), off, off + OFFS);
+      }
+      for (int32_t e : batch)
+        for (int a = 0; a < NEN; ++a) {
+          int32_t n = P.conn[(int64_t)e * NEN + a];
+          if (owner[n] != uid || --last_use[n] > 0) continue;
+          flush_row.push_back(n);
+          flush_slot.push_back(slot_of[n]);
+          free_slots.push_back(slot_of[n]);
+          --live;
+        }
+      batch_visit.push_back((int32_t)visits());
+      batch_flush.push_back((int32_t)flush_row.size());
+    }
+    for (int32_t n : nodes) {
+      owner[n] = -1;
+      touched[n] = 0;
+      last_use[n] = -1;
+    }
+    if (!ok) {
+      batch_visit.resize(mark_b);
+      batch_flush.resize(mark_b);
+      visit_nodes.resize(mark_v * NEN);
+      visit_off.resize(mark_v * OFFS);
+      flush_row.resize(mark_f);
+      flush_slot.resize(mark_f);
+      return false;
+    }
+    unit_batch.push_back((int32_t)(batch_visit.size() - 1));
+    return true;
+  }
+};
+
+// Splits a node set in two by the median of the wider of x and y.
+static void split_xy(const std::vector<double>& coords, std::vector<int32_t>& nodes, std::vector<int32_t>& other) {
+  double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+  for (int32_t n : nodes)
+    for (int d = 0; d < 2; ++d) {
+      lo[d] = std::min(lo[d], coords[(int64_t)n * 3 + d]);
+      hi[d] = std::max(hi[d], coords[(int64_t)n * 3 + d]);
+    }
+  int d = (hi[0] - lo[0] >= hi[1] - lo[1]) ? 0 : 1;
+  std::sort(nodes.begin(), nodes.end(), [&](int32_t a, int32_t b) {
+    double xa = coords[(int64_t)a * 3 + d], xb = coords[(int64_t)b * 3 + d];
+    return xa != xb ? xa < xb : a < b;
+  });
+  size_t h = nodes.size() / 2;
+  other.assign(nodes.begin() + h, nodes.end());
+  nodes.resize(h);
+}
+
+template <typename T>
+static fea_status upload(T** dst, const std::vector<T>& src) {
+  size_t n = std::max<size_t>(src.size(), 1);
+  FEA_CUDA_TRY(cudaMalloc(dst, n * sizeof(T)));
+  if (!src.empty()) FEA_CUDA_TRY(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
   return FEA_OK;
 }
-void plan_destroy(fea_rowowned_plan* plan) { delete plan; }
-bool plan_supports(const fea_rowowned_plan* plan, int, int) { return plan != nullptr; }
-fea_status plan_assemble(const fea_rowowned_plan*, const AsmArgs<float>&, cudaStream_t) {
-  return fail(FEA_ERR_STATE, "row-owned plan unavailable");
+
+static void free_variant(Variant* v) {
+  if (!v) return;
+  cudaFree(v->unit_batch);
+  cudaFree(v->batch_visit);
+  cudaFree(v->batch_flush);
+  cudaFree(v->visit_nodes);
+  cudaFree(v->visit_off);
+  cudaFree(v->flush_row);
+  cudaFree(v->flush_slot);
+  cudaFree(v->fnode);
+  delete v;
+}
+
+static fea_status host_copies(fea_rowowned_plan* P) {
+  if (P->host_ready) return FEA_OK;
+  fea_mesh* m = P->mesh;
+  fea_pattern* p = P->pattern;
+  int64_t N = m->n_node, E = m->n_elem;
+  P->conn.resize((size_t)E * NEN);
+  P->coords.resize((size_t)N * 3);
+  P->rowptr.resize(N + 1);
+  P->colind.resize(p->nnz);
+  P->inc_ptr.resize(N + 1);
+  P->inc_elem.resize((size_t)E * NEN);
+  FEA_CUDA_TRY(cudaStreamSynchronize(m->stream));
+  FEA_CUDA_TRY(cudaMemcpy(P->conn.data(), m->conn, P->conn.size() * 4, cudaMemcpyDeviceToHost));
+  FEA_CUDA_TRY(cudaMemcpy(P->coords.data(), m->coords, P->coords.size() * 8, cudaMemcpyDeviceToHost));
+  FEA_CUDA_TRY(cudaMemcpy(P->rowptr.data(), p->rowptr, P->rowptr.size() * 8, cudaMemcpyDeviceToHost));
+  FEA_CUDA_TRY(cudaMemcpy(P->colind.data(), p->colind, P->colind.size() * 4, cudaMemcpyDeviceToHost));
+  FEA_CUDA_TRY(cudaMemcpy(P->inc_ptr.data(), p->inc_ptr, P->inc_ptr.size() * 8, cudaMemcpyDeviceToHost));
+  FEA_CUDA_TRY(cudaMemcpy(P->inc_elem.data(), p->inc_elem, P->inc_elem.size() * 4, cudaMemcpyDeviceToHost));
+  P->host_ready = true;
+  return FEA_OK;
+}
+
+static fea_status build_variant(fea_rowowned_plan* P, int n_eq, Variant* v) {
+  FEA_TRY(host_copies(P));
+  int64_t N = P->mesh->n_node, E = P->mesh->n_elem;
+  int maxcol = 0;
+  bool unused = false;
+  for (int64_t r = 0; r < N; ++r) {
+    maxcol = std::max<int>(maxcol, (int)(P->rowptr[r + 1] - P->rowptr[r]));
+    if (P->inc_ptr[r + 1] == P->inc_ptr[r]) unused = true;
+  }
+  v->n_eq = n_eq;
+  v->neqs = n_eq | 1;  // odd stride: conflict-free column-wise reads of the row window
+  v->maxcol = maxcol;
+  v->row_stride = ((maxcol + 1) + 3) & ~3;  // slots start 16-byte aligned (bulk zeroing)
+  v->unused_nodes = unused;
+  v->be = batch_elems(n_eq);
+  size_t fixed = smem_fixed(v->be);
+  if (fixed + 4096 > (size_t)SMEM_LIMIT) return FEA_OK;
+  // per slot: its row of row_stride entries of neqs floats
+  const size_t per_slot = sizeof(float) * (size_t)v->row_stride * v->neqs;
+  int n_slots = (int)std::min<size_t>((SMEM_LIMIT - fixed) / per_slot, (NONE - 1) / v->row_stride);
+  if (n_slots < 2 * NEN) return FEA_OK;  // too many equations for this kernel
+  v->n_slots = n_slots;
+  v->smem = fixed + per_slot * (size_t)n_slots;
+  v->smem = (v->smem + 15) & ~(size_t)15;
+  if (v->smem > (size_t)SMEM_LIMIT) return FEA_OK;
+
+  // pencil tiling in x-y, chunks in z, bin edges midway between grid lines
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t n = 0; n < N; ++n)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], P->coords[n * 3 + d]);
+      hi[d] = std::max(hi[d], P->coords[n * 3 + d]);
+    }
+  double vol = std::max(1e-300, (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]));
+  double spacing = std::cbrt(vol / std::max<int64_t>(1, E));  // hex cell width
+  int cols = std::max(1, (int)(0.45 * n_slots));             // node columns per tile (two planes live)
+  int tx0 = std::max(1, (int)std::floor(std::sqrt((double)cols)));
+  int ty0 = std::max(1, cols / tx0);
+  // spread the node planes of each axis evenly over the tiles (fractional widths)
+  auto even = [&](int d, int t) {
+    double planes = std::floor((hi[d] - lo[d]) / spacing + 0.5) + 1.0;
+    double chunks = std::max(1.0, std::ceil(planes / t));
+    return planes / chunks;
+  };
+  const double tx = even(0, tx0), ty = even(1, ty0), tz = even(2, 32);
+  auto bin = [&](double x, double l, double t) { return (int64_t)std::floor(((x - l) / spacing + 0.5) / t); };
+  std::map<std::array<int64_t, 3>, std::vector<int32_t>> units;
+  for (int64_t n = 0; n < N; ++n) {
+    const double* x = &P->coords[n * 3];
+    units[{bin(x[2], lo[2], tz), bin(x[1], lo[1], ty), bin(x[0], lo[0], tx)}].push_back((int32_t)n);
+  }
+  Builder B(*P, n_slots, maxcol, v->be);
+  std::vector<std::vector<int32_t>> work;
+  for (auto& kv : units) work.push_back(std::move(kv.second));
+  int32_t uid = 0;
+  while (!work.empty()) {
+    std::vector<int32_t> nodes = std::move(work.back());
+    work.pop_back();
+    if (B.unit(nodes, uid)) {
+      ++uid;
+      continue;
+    }
+    if (nodes.size() <= 1) return FEA_OK;  // cannot fit even one node's elements
+    std::vector<int32_t> other;
+    split_xy(P->coords, nodes, other);
+    work.push_back(std::move(nodes));
+    work.push_back(std::move(other));
+  }
+  v->n_units = uid;
+  v->n_visits = B.visits();
+  v->n_batches = (int64_t)B.batch_visit.size() - 1;
+  v->n_flush = (int64_t)B.flush_row.size();
+  if (v->n_visits >= INT32_MAX / OFFS) return FEA_OK;
+  // units as (first batch, end batch) pairs, largest first (the kernel deals them out in snake order)
+  std::vector<int32_t> order(uid);
+  std::iota(order.begin(), order.end(), 0);
+  auto cost = [&](int32_t u) { return B.batch_visit[B.unit_batch[u + 1]] - B.batch_visit[B.unit_batch[u]]; };
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cost(a) > cost(b); });
+  std::vector<int32_t> ranges(2 * (size_t)uid);
+  for (int32_t k = 0; k < uid; ++k) {
+    ranges[2 * k] = B.unit_batch[order[k]];
+    ranges[2 * k + 1] = B.unit_batch[order[k] + 1];
+  }
+  FEA_TRY(upload(&v->unit_batch, ranges));
+  FEA_TRY(upload(&v->batch_visit, B.batch_visit));
+  FEA_TRY(upload(&v->batch_flush, B.batch_flush));
+  FEA_TRY(upload(&v->visit_nodes, B.visit_nodes));
+  FEA_TRY(upload(&v->visit_off, B.visit_off));
+  FEA_TRY(upload(&v->flush_row, B.flush_row));
+  FEA_TRY(upload(&v->flush_slot, B.flush_slot));
+  FEA_CUDA_TRY(cudaMalloc(&v->fnode, sizeof(float) * (size_t)N * (3 * n_eq + 3)));
+  v->ok = true;
+  return FEA_OK;
+}
+
+#include "fea_rowowned_kernel.cuh"
+
+}  // namespace ro
+
+fea_status plan_build(fea_mesh* m, fea_pattern* p, fea_rowowned_plan** out) {
+  *out = nullptr;
+  if (m->type != FEA_HEX8 || m->n_elem == 0) return FEA_OK;
+  fea_rowowned_plan* P = new (std::nothrow) fea_rowowned_plan();
+  if (!P) return fail(FEA_ERR_OOM, "host allocation failed");
+  P->mesh = m;
+  P->pattern = p;
+  *out = P;
+  return FEA_OK;
+}
+
+void plan_destroy(fea_rowowned_plan* P) {
+  if (!P) return;
+  for (auto& kv : P->variants) ro::free_variant(kv.second);
+  delete P;
+}
+
+fea_status plan_prepare(fea_rowowned_plan* P, int n_eq, bool* ok) {
+  *ok = false;
+  if (!P) return FEA_OK;
+  std::lock_guard<std::mutex> lk(P->mu);
+  auto it = P->variants.find(n_eq);
+  if (it == P->variants.end()) {
+    ro::Variant* v = new (std::nothrow) ro::Variant();
+    if (!v) return fail(FEA_ERR_OOM, "host allocation failed");
+    fea_status st = ro::build_variant(P, n_eq, v);
+    if (st != FEA_OK) {
+      ro::free_variant(v);
+      return st;
+    }
+    it = P->variants.emplace(n_eq, v).first;
+  }
+  *ok = it->second->ok;
+  return FEA_OK;
+}
+
+namespace ro {
+// Node-major copy of the per-step inputs, so that the (element, equation) threads of one
+// element read contiguous memory: out[n][f n_eq + q] for f = k, s, phi_old, then
+// out[n][3 n_eq + c] = u_c.  One block transposes 32 nodes through shared memory.
+__global__ void k_fields_nodemajor(const float* __restrict__ kd, const float* __restrict__ sr,
+                                   const float* __restrict__ phi, const float* __restrict__ vel, int64_t N, int n_eq,
+                                   float* __restrict__ out) {
+  extern __shared__ float tile[];  // [rec][33]
+  const int rec = 3 * n_eq + 3, lane = threadIdx.x & 31;
+  const int64_t n0 = (int64_t)blockIdx.x * 32, n = n0 + lane;
+  for (int j = threadIdx.x >> 5; j < rec; j += blockDim.x >> 5) {
+    const float* src = j < n_eq       ? kd + (int64_t)j * N
+                       : j < 2 * n_eq ? sr + (int64_t)(j - n_eq) * N
+                       : j < 3 * n_eq ? phi + (int64_t)(j - 2 * n_eq) * N
+                                      : vel + (int64_t)(j - 3 * n_eq) * N;
+    tile[j * 33 + lane] = n < N ? src[n] : 0.f;
+  }
+  __syncthreads();
+  const int cnt = (int)((N - n0) < 32 ? (N - n0) : 32);
+  for (int idx = threadIdx.x; idx < cnt * rec; idx += blockDim.x) {
+    const int node = idx / rec, j = idx - node * rec;
+    out[(n0 + node) * rec + j] = tile[j * 33 + node];
+  }
+}
+}  // namespace ro
+
+fea_status plan_assemble(fea_rowowned_plan* P, const AsmArgs<float>& a, int accumulate, cudaStream_t s) {
+  ro::Variant* v = P->variants.at(a.n_eq);
+  if (v->unused_nodes && !accumulate)
+    FEA_CUDA_TRY(cudaMemsetAsync(a.rhs, 0, sizeof(float) * (size_t)a.n_eq * (size_t)a.n_node, s));
+  const int rec = 3 * a.n_eq + 3;
+  {
+    const size_t tsm = sizeof(float) * rec * 33;
+    FEA_CUDA_TRY(cudaFuncSetAttribute(ro::k_fields_nodemajor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    ro::k_fields_nodemajor<<<(unsigned)((a.n_node + 31) / 32), 256, tsm, s>>>(a.kd, a.sr, a.phi, a.vel, a.n_node,
+                                                                              a.n_eq, v->fnode);
+    FEA_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+  }
+  ro::RoArgs r;
+  r.a = a;
+  r.fnode = v->fnode;
+  r.rec = rec;
+  r.unit_batch = v->unit_batch;
+  r.batch_visit = v->batch_visit;
+  r.batch_flush = v->batch_flush;
+  r.visit_nodes = v->visit_nodes;
+  r.visit_off = v->visit_off;
+  r.flush_row = v->flush_row;
+  r.flush_slot = v->flush_slot;
+  r.n_units = v->n_units;
+  r.n_slots = v->n_slots;
+  r.row_stride = v->row_stride;
+  r.maxcol = v->maxcol;
+  r.neqs = v->neqs;
+  r.accumulate = accumulate;
+  r.be = v->be;
+  auto kern = a.terms == FEA_TERM_ALL ? ro::k_rowowned_hex8<true> : ro::k_rowowned_hex8<false>;
+  FEA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem));
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  unsigned grid = (unsigned)std::max(1, std::min(v->n_units, nsm));
+  kern<<<grid, ro::THREADS, v->smem, s>>>(r);
+  FEA_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return FEA_OK;
 }
 
 }  // namespace fea

@@ -1,0 +1,446 @@
+// fea_rowowned_kernel.cuh -- the row-owned Hex8 kernel (included by fea_rowowned.cu,
+// inside namespace fea::ro, after the plan types).
+//
+// One CTA of THREADS threads walks its work units batch by batch.  Per batch t:
+//   stage     node ids and scatter offsets (plan data) and raw coordinates/velocity
+//             arrive in shared memory by cp.async, issued one and two batches ahead;
+//   geometry  warps 0..ceil(8 nv/32)-1, one thread per (element, Gauss point):
+//             Jacobian, det, J^-T, physical gradients, u.grad N_a,
+//             dV grad N_a . grad N_b, |u|; FP64 Jacobian for badly conditioned points;
+//   matrices  one thread per (element, equation) item, one or two items per thread:
+//             nodal fields from the node-major copy, the element matrix and RHS as sums
+//             over Gauss points (packed FP32x2 FMAs), added with plain load-add-store
+//             into the shared-memory rows (the batch's elements share no owned node);
+//   flush     rows completed by batch t are written to HBM once, with plain stores,
+//             and their slots cleared.
+
+struct RoArgs {
+  AsmArgs<float> a;
+  const int32_t* unit_batch;
+  const int32_t* batch_visit;
+  const int32_t* batch_flush;
+  const int32_t* visit_nodes;
+  const uint16_t* visit_off;
+  const int32_t* flush_row;
+  const int32_t* flush_slot;
+  const float* fnode;  // [N][rec] node-major k, s, phi_old (equation fastest), then u
+  int n_units, n_slots, row_stride, maxcol, neqs, accumulate, be, rec;
+};
+
+// 1-D linear basis at the 2-point Gauss abscissae: l_0(-p) = l_1(p) = AL, l_0(p) = l_1(-p) = BL.
+constexpr float AL = 0.78867513459481288225f;  // (1 + 1/sqrt 3) / 2
+constexpr float BL = 0.21132486540518711775f;  // (1 - 1/sqrt 3) / 2
+constexpr int RAW = 9;                         // per node: xhi[3], xlo[3], u[3]
+
+// N_a at Gauss point g of the trilinear hex: AL^(3-d) BL^d, d = axes where a and g differ.
+__host__ __device__ constexpr float hex_n(int a, int g) {
+  return (((a ^ g) & 1) ? BL : AL) * (((a ^ g) & 2) ? BL : AL) * (((a ^ g) & 4) ? BL : AL);
+}
+
+__host__ __device__ constexpr int sym_index(int a, int b) {  // a <= b
+  return a * NEN - a * (a - 1) / 2 + (b - a);
+}
+
+// Values of a nodal field at the 8 Gauss points by sum factorisation (x, then y, then z).
+__device__ __forceinline__ void interp8(const float v[NEN], float out[NG]) {
+  float tx[2][4], ty[2][2][2];
+#pragma unroll
+  for (int jk = 0; jk < 4; ++jk) {
+    tx[0][jk] = fmaf(AL, v[2 * jk], BL * v[2 * jk + 1]);
+    tx[1][jk] = fmaf(BL, v[2 * jk], AL * v[2 * jk + 1]);
+  }
+#pragma unroll
+  for (int gx = 0; gx < 2; ++gx)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      ty[gx][0][k] = fmaf(AL, tx[gx][2 * k], BL * tx[gx][2 * k + 1]);
+      ty[gx][1][k] = fmaf(BL, tx[gx][2 * k], AL * tx[gx][2 * k + 1]);
+    }
+#pragma unroll
+  for (int gx = 0; gx < 2; ++gx)
+#pragma unroll
+    for (int gy = 0; gy < 2; ++gy) {
+      out[gx + 2 * gy] = fmaf(AL, ty[gx][gy][0], BL * ty[gx][gy][1]);
+      out[gx + 2 * gy + 4] = fmaf(BL, ty[gx][gy][0], AL * ty[gx][gy][1]);
+    }
+}
+
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Per-batch staging buffer in shared memory.
+struct Stage {
+  int32_t* nid;    // [be][8]
+  uint16_t* off;   // [be][OFFS]
+  float* raw;      // [be][8][RAW]
+};
+
+// Issues the copies of the plan data (node ids, offsets) of batch t into buffer s.
+__device__ __forceinline__ void stage_plan(const RoArgs& r, int t, const Stage& s) {
+  const int v0 = r.batch_visit[t], nv = r.batch_visit[t + 1] - v0;
+  const int32_t* vn = r.visit_nodes + (int64_t)v0 * NEN;
+  for (int i = threadIdx.x; i < nv * NEN; i += THREADS) cp_async4(s.nid + i, vn + i);
+  const uint32_t* vo = reinterpret_cast<const uint32_t*>(r.visit_off + (int64_t)v0 * OFFS);
+  uint32_t* so = reinterpret_cast<uint32_t*>(s.off);
+  for (int i = threadIdx.x; i < nv * OFFS / 2; i += THREADS) cp_async4(so + i, vo + i);
+}
+
+// Issues the gathers of the raw node data of batch t (node ids already in buffer s).
+__device__ __forceinline__ void stage_nodes(const RoArgs& r, int t, const Stage& s) {
+  const AsmArgs<float>& A_ = r.a;
+  const int nv = r.batch_visit[t + 1] - r.batch_visit[t];
+  const int64_t N = A_.n_node;
+  for (int i = threadIdx.x; i < nv * NEN * RAW; i += THREADS) {
+    const int node = i / RAW, c = i - node * RAW;
+    const int64_t n = s.nid[node];
+    const float* src = c < 3   ? A_.xhi + (int64_t)c * N + n
+                       : c < 6 ? A_.xlo + (int64_t)(c - 3) * N + n
+                               : r.fnode + n * r.rec + 3 * A_.eq_count + (c - 6);
+    cp_async4(s.raw + i, src);
+  }
+}
+
+// Writes the rows completed by batch tb to HBM and clears their slots: one row per warp
+// step, the lanes walking the row's (equation, column) values with the column fastest
+// (column index len is the RHS entry), so each equation's segment is stored contiguously.
+__device__ __forceinline__ void flush_rows(const RoArgs& r, float* win, int tb) {
+  const AsmArgs<float>& A_ = r.a;
+  const int lane = threadIdx.x & 31, n_eq = A_.eq_count;
+  for (int f = r.batch_flush[tb] + (threadIdx.x >> 5); f < r.batch_flush[tb + 1]; f += THREADS / 32) {
+    const int32_t row = r.flush_row[f];
+    const int base = r.flush_slot[f] * r.row_stride;
+    const int64_t k0 = A_.rowptr[row];
+    const int len = (int)(A_.rowptr[row + 1] - k0);
+    const int w = len + 1;
+    int q = lane / w, c = lane - q * w;  // position of this lane, advanced by 32 values per step
+    const int step_q = 32 / w, step_c = 32 - step_q * w;
+    // separate loops: with the accumulate test inside, the compiler may read *dst unconditionally
+    if (!r.accumulate) {
+#pragma unroll 4
+      for (int idx = lane; idx < w * n_eq; idx += 32) {
+        const float v = win[(base + (c < len ? c : r.maxcol)) * r.neqs + q];
+        float* dst = c < len ? A_.values + (int64_t)(A_.eq0 + q) * A_.nnz + k0 + c
+                             : A_.rhs + (int64_t)(A_.eq0 + q) * A_.n_node + row;
+        __stcs(dst, v);  // streaming store: written once, not re-read by this kernel
+        q += step_q;
+        c += step_c;
+        if (c >= w) {
+          c -= w;
+          ++q;
+        }
+      }
+    } else {
+      for (int idx = lane; idx < w * n_eq; idx += 32) {
+        const float v = win[(base + (c < len ? c : r.maxcol)) * r.neqs + q];
+        float* dst = c < len ? A_.values + (int64_t)(A_.eq0 + q) * A_.nnz + k0 + c
+                             : A_.rhs + (int64_t)(A_.eq0 + q) * A_.n_node + row;
+        *dst += v;
+        q += step_q;
+        c += step_c;
+        if (c >= w) {
+          c -= w;
+          ++q;
+        }
+      }
+    }
+    __syncwarp();
+    // clear the slot (contiguous, 16-byte aligned: row_stride is a multiple of 4)
+    float4* z = reinterpret_cast<float4*>(win + base * r.neqs);
+    for (int i = lane; i < r.row_stride * r.neqs / 4; i += 32) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Geometry of element ge at Gauss point g of the batch in S into geo; all 32 lanes of the
+// calling warp must call it (the element volume is a shuffle reduction over 8 lanes).
+__device__ __forceinline__ void geometry(const RoArgs& r, const Stage& S, float* geo, int ge, int g, bool gact) {
+  const AsmArgs<float>& A_ = r.a;
+  float dv = 0.f, un = 0.f, ua[NEN], gr[NEN][3];
+  if (gact) {
+    const float pp = 0.57735026918962576451f;
+    const float xi[3] = {(g & 1) ? pp : -pp, (g & 2) ? pp : -pp, (g & 4) ? pp : -pp};
+    float J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, dN[NEN][3], ug[3] = {0, 0, 0};
+    const float* d = S.raw + ge * NEN * RAW;
+#pragma unroll
+    for (int a = 0; a < NEN; ++a) {
+      float Na;
+      shape<FEA_HEX8>(a, xi, Na, dN[a]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float xa = (d[a * RAW + i] - d[i]) + (d[a * RAW + 3 + i] - d[3 + i]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) J[i][j] = fmaf(xa, dN[a][j], J[i][j]);
+        ug[i] = fmaf(Na, d[a * RAW + 6 + i], ug[i]);
+      }
+    }
+    float det = det3(J), Gt[3][3];
+    inv_transpose3(J, det, Gt);
+    // condition estimate |J|_F |J^-1|_F / 3; above the threshold the Jacobian is redone in FP64
+    float nj = 0.f, ni = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        nj = fmaf(J[i][j], J[i][j], nj);
+        ni = fmaf(Gt[i][j], Gt[i][j], ni);
+      }
+    if (!(det > 0.f) || nj * ni > 9.0f * (float)(A_.kappa_threshold * A_.kappa_threshold)) {
+      const int32_t* ids = S.nid + ge * NEN;
+      const double pd = 0.57735026918962576451;
+      const double xid[3] = {(g & 1) ? pd : -pd, (g & 2) ? pd : -pd, (g & 4) ? pd : -pd};
+      double Jd[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Gd[3][3];
+      for (int a = 0; a < NEN; ++a) {
+        double Nd, dNd[3];
+        shape<FEA_HEX8>(a, xid, Nd, dNd);
+        for (int i = 0; i < 3; ++i) {
+          double xa = A_.coords[(int64_t)ids[a] * 3 + i] - A_.coords[(int64_t)ids[0] * 3 + i];
+          for (int j = 0; j < 3; ++j) Jd[i][j] += xa * dNd[j];
+        }
+      }
+      const double dd = det3(Jd);
+      if (!(dd > 0.0)) atomicOr(A_.status, ST_INVERTED);
+      inv_transpose3(Jd, dd, Gd);
+      det = (float)dd;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Gt[i][j] = (float)Gd[i][j];
+    }
+#pragma unroll
+    for (int a = 0; a < NEN; ++a) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) gr[a][i] = Gt[i][0] * dN[a][0] + Gt[i][1] * dN[a][1] + Gt[i][2] * dN[a][2];
+      ua[a] = ug[0] * gr[a][0] + ug[1] * gr[a][1] + ug[2] * gr[a][2];
+    }
+    dv = det;  // Gauss weight 1
+    un = sqrtf(ug[0] * ug[0] + ug[1] * ug[1] + ug[2] * ug[2]);
+  }
+  float vol = dv;
+  vol += __shfl_xor_sync(0xffffffffu, vol, 1);
+  vol += __shfl_xor_sync(0xffffffffu, vol, 2);
+  vol += __shfl_xor_sync(0xffffffffu, vol, 4);
+  if (gact) {
+    const float h = cbrtf(vol);
+    float4* G4 = reinterpret_cast<float4*>(geo + ge * GEO_ELEM + g * GEO);
+    float gv[GEO];
+    gv[0] = dv;
+    gv[1] = 2.f * un / h;
+#pragma unroll
+    for (int a = 0; a < NEN; ++a) gv[2 + a] = ua[a];
+#pragma unroll
+    for (int a = 0; a < NEN; ++a)
+#pragma unroll
+      for (int b = a; b < NEN; ++b)
+        gv[10 + sym_index(a, b)] = dv * (gr[a][0] * gr[b][0] + gr[a][1] * gr[b][1] + gr[a][2] * gr[b][2]);
+    gv[46] = gv[47] = 0.f;
+#pragma unroll
+    for (int k2 = 0; k2 < GEO / 4; ++k2) G4[k2] = make_float4(gv[4 * k2], gv[4 * k2 + 1], gv[4 * k2 + 2], gv[4 * k2 + 3]);
+    if (g == 0) geo[ge * GEO_ELEM + NG * GEO] = 4.f / (h * h);
+  }
+}
+
+// Nodal k, s, phi_old of equation q at the nodes of batch element el, from the node-major copy
+// (the threads of one element read consecutive equations: contiguous memory).
+__device__ __forceinline__ void load_fields(const RoArgs& r, const Stage& S, int el, int q, float kn[NEN],
+                                            float sn[NEN], float pn[NEN]) {
+  const int n_eq = r.a.eq_count;
+#pragma unroll
+  for (int a = 0; a < NEN; ++a) {
+    const float* F = r.fnode + (int64_t)S.nid[el * NEN + a] * r.rec + q;
+    kn[a] = __ldg(F);
+    sn[a] = __ldg(F + n_eq);
+    pn[a] = __ldg(F + 2 * n_eq);
+  }
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
+  extern __shared__ __align__(16) float sm_ro[];
+  const AsmArgs<float>& A_ = r.a;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int be = r.be;
+  const int win_floats = r.n_slots * r.row_stride * r.neqs;
+  float* win = sm_ro;
+  float* geo = win + ((win_floats + 3) & ~3);
+  float* const stage0 = geo + be * GEO_ELEM;
+  const int stage_floats = be * (NEN * RAW + NEN + OFFS / 2);
+  auto stage = [&](int b) {  // staging buffer b in {0, 1}, addressed without a local array
+    float* p = stage0 + b * stage_floats;
+    Stage s;
+    s.raw = p;
+    s.nid = reinterpret_cast<int32_t*>(p + be * NEN * RAW);
+    s.off = reinterpret_cast<uint16_t*>(p + be * NEN * RAW + be * NEN);
+    return s;
+  };
+  const float inv_dt = (float)(1.0 / A_.dt);
+  const bool t_mass = A_.terms & FEA_TERM_MASS, t_conv = A_.terms & FEA_TERM_CONV,
+             t_diff = A_.terms & FEA_TERM_DIFF, t_reac = A_.terms & FEA_TERM_REAC,
+             t_supg = A_.terms & FEA_TERM_SUPG;
+  const int n_eq = A_.eq_count;
+
+  for (int i = tid; i < win_floats; i += THREADS) win[i] = 0.f;
+
+  // Units are sorted by size; CTA b takes units b, 2G-1-b, 2G+b, ... (snake order).
+  const int G = gridDim.x;
+  for (int k = 0;; ++k) {
+    const int u = (k & 1) ? (k + 1) * G - 1 - (int)blockIdx.x : k * G + (int)blockIdx.x;
+    if (u >= r.n_units) break;
+    const int t0 = r.unit_batch[2 * u], t1 = r.unit_batch[2 * u + 1];
+    // prologue: batch t0 into buffer 0, plan data of t0+1 into buffer 1
+    __syncthreads();
+    stage_plan(r, t0, stage(0));
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    stage_nodes(r, t0, stage(0));
+    cp_async_commit();
+    if (t0 + 1 < t1) stage_plan(r, t0 + 1, stage(1));
+    cp_async_commit();
+    for (int t = t0; t < t1; ++t) {
+      const Stage S = stage((t - t0) & 1);
+      const Stage Sn = stage((t - t0 + 1) & 1);
+      const int nv = r.batch_visit[t + 1] - r.batch_visit[t];
+      const int items = nv * n_eq;
+      cp_async_wait_all();  // raw node data of t, plan data of t+1
+      __syncthreads();
+      if (t + 1 < t1) stage_nodes(r, t + 1, Sn);
+      cp_async_commit();
+      // geometry of batch t
+      const int gw = (nv * NG + 31) / 32;
+      if (warp < gw) geometry(r, S, geo, tid >> 3, tid & 7, (tid >> 3) < nv);
+      __syncthreads();
+      float kn[NEN], sn[NEN], pn[NEN];
+      if (tid < items) load_fields(r, S, tid / n_eq, tid % n_eq, kn, sn, pn);
+      // element matrices: items tid, tid + THREADS (element = item / n_eq, equation = item % n_eq)
+      for (int item = tid; item < items; item += THREADS) {
+        const int el = item / n_eq, q = item - el * n_eq;
+        const float* Ge = geo + el * GEO_ELEM;
+        const float ck = Ge[NG * GEO];
+        const uint32_t* eo = reinterpret_cast<const uint32_t*>(S.off + el * OFFS);
+        float kg[NG], sg[NG], pg[NG];
+        interp8(kn, kg);
+        interp8(sn, sg);
+        interp8(pn, pg);
+        if (item + THREADS < items)  // prefetch the next item's fields while this one computes
+          load_fields(r, S, (item + THREADS) / n_eq, (item + THREADS) % n_eq, kn, sn, pn);
+        float2 Am[NEN][NEN / 2], Dm[18], bv2[NEN / 2];
+#pragma unroll
+        for (int a = 0; a < NEN; ++a)
+#pragma unroll
+          for (int b = 0; b < NEN / 2; ++b) Am[a][b] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k2 = 0; k2 < 18; ++k2) Dm[k2] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < NEN / 2; ++a) bv2[a] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          const float4* G4 = reinterpret_cast<const float4*>(Ge + g * GEO);
+          float gv[GEO];
+#pragma unroll
+          for (int k2 = 0; k2 < GEO / 4 - 1; ++k2) {
+            const float4 x = G4[k2];
+            gv[4 * k2] = x.x;
+            gv[4 * k2 + 1] = x.y;
+            gv[4 * k2 + 2] = x.z;
+            gv[4 * k2 + 3] = x.w;
+          }
+          {
+            const float4 x = G4[GEO / 4 - 1];
+            gv[GEO - 4] = x.x;
+            gv[GEO - 3] = x.y;
+          }
+          const float dv = gv[0];
+          const float den = fmaf(ck, kg[g], gv[1] + sg[g]);
+          const float tau = den > 0.f ? __fdividef(1.f, den) : 0.f;
+          const float dvt = t_supg ? dv * tau : 0.f;
+          const float sigs = inv_dt + sg[g];
+          float P[NEN], Q[NEN];
+          if (FULL) {
+            // all terms: dV (N_a + tau u.gradN_a)((1/dt + s) N_b + u.gradN_b), one rank-1 product
+#pragma unroll
+            for (int a = 0; a < NEN; ++a) {
+              P[a] = fmaf(dvt, gv[2 + a], dv * hex_n(a, g));
+              Q[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
+            }
+#pragma unroll
+            for (int a = 0; a < NEN; ++a) {
+              const float2 pa = make_float2(P[a], P[a]);
+#pragma unroll
+              for (int b = 0; b < NEN / 2; ++b) Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
+            }
+          } else {
+            // dV N_a (sig N_b + [conv] u.gradN_b) + [supg] dV tau u.gradN_a ((1/dt + s) N_b + u.gradN_b)
+            const float sig = (t_mass ? inv_dt : 0.f) + (t_reac ? sg[g] : 0.f);
+            float Ps[NEN], R[NEN];
+#pragma unroll
+            for (int a = 0; a < NEN; ++a) {
+              P[a] = dv * hex_n(a, g);
+              Ps[a] = dvt * gv[2 + a];
+              Q[a] = sig * hex_n(a, g) + (t_conv ? gv[2 + a] : 0.f);
+              R[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
+            }
+#pragma unroll
+            for (int a = 0; a < NEN; ++a) {
+              const float2 pa = make_float2(P[a], P[a]), ps = make_float2(Ps[a], Ps[a]);
+#pragma unroll
+              for (int b = 0; b < NEN / 2; ++b) {
+                Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
+                Am[a][b] = __ffma2_rn(ps, make_float2(R[2 * b], R[2 * b + 1]), Am[a][b]);
+              }
+            }
+            if (!t_mass) {
+#pragma unroll
+              for (int a = 0; a < NEN; ++a) P[a] = 0.f;
+            }
+#pragma unroll
+            for (int a = 0; a < NEN; ++a) P[a] += Ps[a];
+          }
+          if (t_diff) {
+            const float2 k2v = make_float2(kg[g], kg[g]);
+#pragma unroll
+            for (int k2 = 0; k2 < 18; ++k2) Dm[k2] = __ffma2_rn(k2v, make_float2(gv[10 + 2 * k2], gv[11 + 2 * k2]), Dm[k2]);
+          }
+          const float2 pdt = make_float2(pg[g] * inv_dt, pg[g] * inv_dt);
+#pragma unroll
+          for (int a = 0; a < NEN / 2; ++a) bv2[a] = __ffma2_rn(make_float2(P[2 * a], P[2 * a + 1]), pdt, bv2[a]);
+        }
+        // add into the shared-memory rows (offsets are in row-window entries of neqs floats).
+        // The elements of a batch share no owned node, so no two threads touch the same word.
+        // Per matrix row: the 9 words (8 columns and the RHS) are distinct, so all 9 are
+        // loaded before any is stored (the compiler cannot prove that and would otherwise
+        // serialise every load behind the previous store).
+#pragma unroll
+        for (int a = 0; a < NEN; ++a) {
+          const uint32_t rw = eo[(NEN * NEN + a) / 2];
+          const uint32_t ro = (a & 1) ? (rw >> 16) : (rw & 0xFFFFu);
+          if (ro == NONE) continue;
+          float* p[NEN + 1];
+          float add[NEN + 1];
+#pragma unroll
+          for (int b = 0; b < NEN; b += 2) {
+            const uint32_t w2 = eo[(a * NEN + b) / 2];
+            const int i0 = a <= b ? sym_index(a, b) : sym_index(b, a);
+            const int i1 = a <= b + 1 ? sym_index(a, b + 1) : sym_index(b + 1, a);
+            p[b] = win + (int)(w2 & 0xFFFFu) * r.neqs + q;
+            p[b + 1] = win + (int)(w2 >> 16) * r.neqs + q;
+            add[b] = Am[a][b / 2].x + ((i0 & 1) ? Dm[i0 >> 1].y : Dm[i0 >> 1].x);
+            add[b + 1] = Am[a][b / 2].y + ((i1 & 1) ? Dm[i1 >> 1].y : Dm[i1 >> 1].x);
+          }
+          p[NEN] = win + (int)ro * r.neqs + q;
+          add[NEN] = (a & 1) ? bv2[a / 2].y : bv2[a / 2].x;
+          float old[NEN + 1];
+#pragma unroll
+          for (int b = 0; b <= NEN; ++b) old[b] = *p[b];
+#pragma unroll
+          for (int b = 0; b <= NEN; ++b) *p[b] = old[b] + add[b];
+        }
+      }
+      __syncthreads();
+      // rows completed by batch t; plan data of t+2 into the buffer that batch t used
+      flush_rows(r, win, t);
+      if (t + 2 < t1) stage_plan(r, t + 2, S);
+      cp_async_commit();
+    }
+  }
+}

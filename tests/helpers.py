@@ -70,11 +70,12 @@ def widen(fields: G.Fields, precision: int) -> G.Fields:
 def row_errors(rowptr, vals, ref, absref=None):
     """Per-row relative Frobenius error ||A_i - A*_i|| / ||A*_i|| for every equation."""
     vals = np.asarray(vals, np.float64)
-    d2 = np.add.reduceat((vals - ref) ** 2, rowptr[:-1], axis=1) if vals.shape[1] else np.zeros((vals.shape[0], 0))
-    r2 = np.add.reduceat(ref ** 2, rowptr[:-1], axis=1) if ref.shape[1] else np.zeros((ref.shape[0], 0))
-    empty = np.diff(rowptr) == 0
-    d2[:, empty] = 0.0
-    r2[:, empty] = 1.0
+    full = np.diff(rowptr) > 0
+    d2 = np.zeros((ref.shape[0], rowptr.size - 1))
+    r2 = np.ones((ref.shape[0], rowptr.size - 1))
+    if full.any():  # reduceat over the starts of the non-empty rows only
+        d2[:, full] = np.add.reduceat((vals - ref) ** 2, rowptr[:-1][full], axis=1)
+        r2[:, full] = np.add.reduceat(ref ** 2, rowptr[:-1][full], axis=1)
     return np.sqrt(d2 / r2)
 
 

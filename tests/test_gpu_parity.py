@@ -77,6 +77,13 @@ def test_accumulate_adds(case):
     v2, r2 = run.assemble(w.fields, fea.FEA_F64_PLAIN, accumulate=1, out=(v1.clone(), r1.clone()))
     assert np.allclose(v2.cpu().numpy(), 2 * v1.cpu().numpy(), rtol=1e-13, atol=0)
     assert np.allclose(r2.cpu().numpy(), 2 * r1.cpu().numpy(), rtol=1e-13, atol=0)
+    for scatter in (fea.FEA_SCATTER_AUTO, fea.FEA_SCATTER_ATOMIC):
+        v1, r1 = run.assemble(w.fields, fea.FEA_F32_FUSED, scatter=scatter)
+        v2, r2 = run.assemble(w.fields, fea.FEA_F32_FUSED, scatter=scatter, accumulate=1,
+                              out=(v1.clone(), r1.clone()))
+        scale = np.abs(v1.cpu().numpy()).max()
+        assert np.abs(v2.cpu().numpy() - 2 * v1.cpu().numpy()).max() <= 1e-6 * scale
+        assert np.abs(r2.cpu().numpy() - 2 * r1.cpu().numpy()).max() <= 1e-6 * np.abs(r1.cpu().numpy()).max()
 
 
 def test_host_entry_point(case):
