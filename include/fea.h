@@ -174,6 +174,26 @@ FEA_API fea_status fea_assemble_host(fea_mesh* mesh, const fea_pattern* pattern,
 FEA_API fea_status fea_pack_plan(const int64_t* count_by_type, int32_t n_types, int32_t vector_size, int64_t* packs,
                          int64_t* pads);
 
+/*
+ * fea_csr_rowptr_noalloc -- CSR row pointers from per-row counts, allocating nothing.
+ * The paper has no counterpart.  It is the row-pointer step of fea_pattern_build, offered
+ * to callers that cannot let a library allocate device memory: for example a program whose
+ * device memory all belongs to its own pool or arena.
+ *   counts  [n] int32 DEVICE pointer, caller-owned: counts[i] >= 0 columns in row i
+ *   rowptr  [n+1] int64 DEVICE pointer, caller-owned output:
+ *           rowptr[0] = 0, rowptr[i+1] = rowptr[i] + counts[i]
+ *   stream  cudaStream_t the work is enqueued on (NULL = legacy default stream); the call
+ *           returns without waiting.
+ * Limit: n <= 33,554,432 rows; a larger n fails with FEA_ERR_TOO_LARGE and does no work.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its partial sums live in
+ * one fixed 128 KiB array per GPU that every call in the process shares; each call rewrites
+ * the part it uses, so nothing has to be cleared, but calls whose work overlaps on the GPU
+ * (other streams, other threads) race on that array and must be serialised by the caller.
+ * The first call on each GPU looks up the array's device address with that GPU current;
+ * make that first call before any stream capture.
+ */
+FEA_API fea_status fea_csr_rowptr_noalloc(const int32_t* counts, int64_t n, int64_t* rowptr, void* stream);
+
 /* Thread-local message describing the last failure of a call on this thread. */
 FEA_API const char* fea_last_error(void);
 /* Number of CUDA kernels this library has launched in this process so far. */

@@ -26,7 +26,7 @@ NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27}
 # Every symbol include/fea.h declares (checked by the tests).
 EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_destroy", "fea_mesh_set_stream", "fea_sync",
            "fea_pattern_build", "fea_pattern_get", "fea_pattern_destroy", "fea_assemble", "fea_assemble_host",
-           "fea_pack_plan", "fea_last_error", "fea_kernel_launches", "fea_version"]
+           "fea_pack_plan", "fea_csr_rowptr_noalloc", "fea_last_error", "fea_kernel_launches", "fea_version"]
 
 
 class FeaError(RuntimeError):
@@ -65,6 +65,7 @@ def lib(path: str = LIB_PATH):
         L.fea_assemble.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(fea_assemble_opts), vp, vp]
         L.fea_assemble_host.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(fea_assemble_opts), vp, vp]
         L.fea_pack_plan.argtypes = [vp, i32, i32, vp, vp]
+        L.fea_csr_rowptr_noalloc.argtypes = [vp, i64, vp, vp]
         L.fea_last_error.restype = C.c_char_p
         L.fea_version.restype = C.c_int32
         L.fea_kernel_launches.restype = C.c_int64
@@ -170,6 +171,11 @@ def fea_pack_plan(count_by_type, vector_size: int):
     _check(lib().fea_pack_plan(counts.ctypes.data, counts.size, int(vector_size), packs.ctypes.data,
                                pads.ctypes.data))
     return packs, pads
+
+
+def fea_csr_rowptr_noalloc(counts, n: int, rowptr, stream=None):
+    """rowptr[n+1] (int64 CUDA tensor) from counts[n] (int32 CUDA tensor) without device allocation."""
+    _check(lib().fea_csr_rowptr_noalloc(_ptr(counts), int(n), _ptr(rowptr), _stream_ptr(stream)))
 
 
 def fea_last_error() -> str:
