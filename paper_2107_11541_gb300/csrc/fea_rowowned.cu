@@ -34,6 +34,8 @@ namespace ro {
 constexpr int NEN = 8, NG = 8;
 constexpr int BEMAX = 24;               // elements per batch at most: geometry uses <= 6 warps, >= 2 flush
 constexpr int THREADS = 256;            // 8 warps
+constexpr int ROUNDS = 4;               // scatter rounds: local rows a and a + 4 in round a & 3
+constexpr int round_of(int a) { return a & 3; }
 constexpr int LOOKAHEAD = 64;           // sweep positions scanned when colouring a batch
 constexpr int GEO = 48;                 // floats per Gauss point: dv, cu, ua[8], Gd[36], pad[2]
 constexpr int GEO_ELEM = NG * GEO + 4;  // + ck (4/h^2) and padding
@@ -51,8 +53,7 @@ struct Variant {
   int32_t* batch_flush = nullptr;  // [n_batches+1]
   int32_t* visit_nodes = nullptr;  // [n_visits][NEN] node ids of the visited element
   uint16_t* visit_off = nullptr;   // [n_visits][OFFS]
-  int32_t* flush_row = nullptr;    // [n_flush]
-  int32_t* flush_slot = nullptr;   // [n_flush]
+  int32_t* flush_meta = nullptr;   // [n_flush][4] row, slot entry base, first CSR position, row length
   float* fnode = nullptr;          // [N][3 n_eq + 3] node-major k, s, phi_old (equation fastest) and u
   bool ok = false;
 };
@@ -99,15 +100,17 @@ struct Builder {
   std::vector<int32_t> owner;      // unit being simulated that owns the node, or -1
   std::vector<int32_t> slot_of;    // node -> slot during simulation
   std::vector<int32_t> last_use;   // node -> last element position in the unit
-  std::vector<uint8_t> touched;
+  std::vector<uint8_t> touched;    // node already holds a slot
+  std::vector<uint8_t> round_mask; // scatter rounds in which the current batch writes the node
   // outputs
-  std::vector<int32_t> unit_batch{0}, batch_visit{0}, batch_flush{0}, visit_nodes, flush_row, flush_slot;
+  std::vector<int32_t> unit_batch{0}, batch_visit{0}, batch_flush{0}, visit_nodes, flush_meta;
+  int64_t flushes() const { return (int64_t)flush_meta.size() / 4; }
   int64_t visits() const { return (int64_t)visit_nodes.size() / NEN; }
   std::vector<uint16_t> visit_off;
 
   Builder(const fea_rowowned_plan& p, int slots, int mc, int batch)
       : P(p), N((int64_t)p.rowptr.size() - 1), E((int64_t)p.conn.size() / NEN), n_slots(slots), maxcol(mc),
-        row_stride(((mc + 1) + 3) & ~3), be(batch), owner(N, -1), slot_of(N, -1), last_use(N, -1), touched(N, 0) {}
+        row_stride(((mc + 1) + 3) & ~3), be(batch), owner(N, -1), slot_of(N, -1), last_use(N, -1), touched(N, 0), round_mask(N, 0) {}
 
   double cz(int32_t e, int d) const {
     double s = 0;
@@ -147,17 +150,19 @@ struct Builder {
         if (owner[n] == uid) last_use[n] = (last_use[n] < 0 ? 0 : last_use[n]) + 1;
       }
 
-    size_t mark_b = batch_visit.size(), mark_v = (size_t)visits(), mark_f = flush_row.size();
+    size_t mark_b = batch_visit.size(), mark_v = (size_t)visits(), mark_f = flush_meta.size();
     std::vector<int32_t> free_slots(n_slots);
     for (int i = 0; i < n_slots; ++i) free_slots[i] = n_slots - 1 - i;
     std::vector<uint8_t> done(seq.size(), 0);
     int live = 0;
     size_t head = 0;
     bool ok = true;
-    std::vector<int32_t> fresh, batch, in_batch;
+    std::vector<int32_t> fresh, batch, in_batch, completed, flushing;
     while (head < seq.size()) {
-      // Greedy colouring in a look-ahead window of the sweep: the elements of a
-      // batch share no owned node, so the kernel accumulates them without atomics.
+      // Greedy batching in a look-ahead window of the sweep.  The kernel adds local rows
+      // a and a+4 of every element in scatter round a & 3, with a barrier between rounds,
+      // so two elements of a batch may share an owned node only if they reach it in
+      // different rounds; then no two threads update the same word at the same time.
       fresh.clear();
       batch.clear();
       int scanned = 0;
@@ -169,23 +174,28 @@ struct Builder {
         int k = 0;
         for (int a = 0; a < NEN; ++a) {
           if (owner[ce[a]] != uid) continue;
-          if (touched[ce[a]] == 2) clash = true;
-          if (!touched[ce[a]]) ++k;
+          if (round_mask[ce[a]] & (1u << round_of(a))) clash = true;
+          if (!touched[ce[a]] && !round_mask[ce[a]]) ++k;
         }
         if (clash) continue;
         if (live + (int)fresh.size() + k > n_slots) break;
         for (int a = 0; a < NEN; ++a) {
           if (owner[ce[a]] != uid) continue;
-          if (!touched[ce[a]]) fresh.push_back(ce[a]);
-          touched[ce[a]] = 2;  // 2: in the current batch, 1: live from an earlier batch
+          if (!touched[ce[a]] && !round_mask[ce[a]]) fresh.push_back(ce[a]);
+          round_mask[ce[a]] |= (uint8_t)(1u << round_of(a));
           in_batch.push_back(ce[a]);
         }
         done[i] = 1;
         batch.push_back(seq[i]);
       }
-      for (int32_t n : in_batch) touched[n] = 1;
+      for (int32_t n : in_batch) {
+        touched[n] = 1;
+        round_mask[n] = 0;
+      }
       in_batch.clear();
-      if (batch.empty()) { ok = false; break; }
+      if (batch.empty() && flushing.empty()) { ok = false; break; }
+      // An empty batch (every candidate waits for a slot still being written out) only
+      // lets the rows of the previous batch be flushed; its slots are free afterwards.
       while (head < seq.size() && done[head]) ++head;
       for (int32_t n : fresh) {
         slot_of[n] = free_slots.back();
@@ -208,13 +218,18 @@ struct Builder {
         for (int a = 0; a < NEN; ++a) {
           int32_t n = P.conn[(int64_t)e * NEN + a];
           if (owner[n] != uid || --last_use[n] > 0) continue;
-          flush_row.push_back(n);
-          flush_slot.push_back(slot_of[n]);
-          free_slots.push_back(slot_of[n]);
-          --live;
+          const int64_t k0 = P.rowptr[n];
+          flush_meta.insert(flush_meta.end(), {n, slot_of[n] * row_stride, (int32_t)k0, (int32_t)(P.rowptr[n + 1] - k0)});
+          completed.push_back(slot_of[n]);
         }
+      // A row completed by batch b is written out while batch b+1 computes, so its slot
+      // is free again from batch b+2 on.
+      free_slots.insert(free_slots.end(), flushing.begin(), flushing.end());
+      live -= (int)flushing.size();
+      flushing.swap(completed);
+      completed.clear();
       batch_visit.push_back((int32_t)visits());
-      batch_flush.push_back((int32_t)flush_row.size());
+      batch_flush.push_back((int32_t)flushes());
     }
     for (int32_t n : nodes) {
       owner[n] = -1;
@@ -226,8 +241,7 @@ struct Builder {
       batch_flush.resize(mark_b);
       visit_nodes.resize(mark_v * NEN);
       visit_off.resize(mark_v * OFFS);
-      flush_row.resize(mark_f);
-      flush_slot.resize(mark_f);
+      flush_meta.resize(mark_f);
       return false;
     }
     unit_batch.push_back((int32_t)(batch_visit.size() - 1));
@@ -268,8 +282,7 @@ static void free_variant(Variant* v) {
   cudaFree(v->batch_flush);
   cudaFree(v->visit_nodes);
   cudaFree(v->visit_off);
-  cudaFree(v->flush_row);
-  cudaFree(v->flush_slot);
+  cudaFree(v->flush_meta);
   cudaFree(v->fnode);
   delete v;
 }
@@ -332,7 +345,11 @@ static fea_status build_variant(fea_rowowned_plan* P, int n_eq, Variant* v) {
   double vol = std::max(1e-300, (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]));
   double spacing = std::cbrt(vol / std::max<int64_t>(1, E));  // hex cell width
   int cols = std::max(1, (int)(0.45 * n_slots));             // node columns per tile (two planes live)
-  int tx0 = std::max(1, (int)std::floor(std::sqrt((double)cols)));
+  // tiles about 3x wider in x (the fastest node-id direction) than in y: the rows a batch
+  // completes then form longer runs of consecutive CSR rows, which HBM writes much faster,
+  // for about the same halo as a square tile of the same area
+  const double aspect = 3.0;
+  int tx0 = std::max(1, (int)std::floor(std::sqrt((double)cols * aspect)));
   int ty0 = std::max(1, cols / tx0);
   // spread the node planes of each axis evenly over the tiles (fractional widths)
   auto even = [&](int d, int t) {
@@ -367,7 +384,7 @@ static fea_status build_variant(fea_rowowned_plan* P, int n_eq, Variant* v) {
   v->n_units = uid;
   v->n_visits = B.visits();
   v->n_batches = (int64_t)B.batch_visit.size() - 1;
-  v->n_flush = (int64_t)B.flush_row.size();
+  v->n_flush = B.flushes();
   if (v->n_visits >= INT32_MAX / OFFS) return FEA_OK;
   // units as (first batch, end batch) pairs, largest first (the kernel deals them out in snake order)
   std::vector<int32_t> order(uid);
@@ -384,8 +401,7 @@ static fea_status build_variant(fea_rowowned_plan* P, int n_eq, Variant* v) {
   FEA_TRY(upload(&v->batch_flush, B.batch_flush));
   FEA_TRY(upload(&v->visit_nodes, B.visit_nodes));
   FEA_TRY(upload(&v->visit_off, B.visit_off));
-  FEA_TRY(upload(&v->flush_row, B.flush_row));
-  FEA_TRY(upload(&v->flush_slot, B.flush_slot));
+  FEA_TRY(upload(&v->flush_meta, B.flush_meta));
   FEA_CUDA_TRY(cudaMalloc(&v->fnode, sizeof(float) * (size_t)N * (3 * n_eq + 3)));
   v->ok = true;
   return FEA_OK;
@@ -479,8 +495,7 @@ fea_status plan_assemble(fea_rowowned_plan* P, const AsmArgs<float>& a, int accu
   r.batch_flush = v->batch_flush;
   r.visit_nodes = v->visit_nodes;
   r.visit_off = v->visit_off;
-  r.flush_row = v->flush_row;
-  r.flush_slot = v->flush_slot;
+  r.flush_meta = reinterpret_cast<const int4*>(v->flush_meta);
   r.n_units = v->n_units;
   r.n_slots = v->n_slots;
   r.row_stride = v->row_stride;

@@ -10,9 +10,14 @@
 //   matrices  one thread per (element, equation) item, one or two items per thread:
 //             nodal fields from the node-major copy, the element matrix and RHS as sums
 //             over Gauss points (packed FP32x2 FMAs), added with plain load-add-store
-//             into the shared-memory rows (the batch's elements share no owned node);
-//   flush     rows completed by batch t are written to HBM once, with plain stores,
-//             and their slots cleared.
+//             into the shared-memory rows in four rounds (local rows a and a+4 in round
+//             a & 3, a barrier after each): elements of a batch share an owned node
+//             only if they reach it in different rounds;
+//   flush     between its first and second item, each warp writes its share of the
+//             rows completed by batch t-1 to HBM once, with plain stores, and clears
+//             their slots (the stores overlap the other warps' arithmetic).  The plan
+//             hands such a slot out again from batch t+1 on; the rows the unit's last
+//             batch completes are written once it ends.
 
 struct RoArgs {
   AsmArgs<float> a;
@@ -21,8 +26,7 @@ struct RoArgs {
   const int32_t* batch_flush;
   const int32_t* visit_nodes;
   const uint16_t* visit_off;
-  const int32_t* flush_row;
-  const int32_t* flush_slot;
+  const int4* flush_meta;  // [n_flush] {row, slot entry base, first CSR position, row length}
   const float* fnode;  // [N][rec] node-major k, s, phi_old (equation fastest), then u
   int n_units, n_slots, row_stride, maxcol, neqs, accumulate, be, rec;
 };
@@ -69,6 +73,10 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) 
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
@@ -104,22 +112,49 @@ __device__ __forceinline__ void stage_nodes(const RoArgs& r, int t, const Stage&
   }
 }
 
-// Writes the rows completed by batch tb to HBM and clears their slots: one row per warp
-// step, the lanes walking the row's (equation, column) values with the column fastest
-// (column index len is the RHS entry), so each equation's segment is stored contiguously.
-__device__ __forceinline__ void flush_rows(const RoArgs& r, float* win, int tb) {
+// Writes the rows completed by batch tb to HBM and clears their slots; warp w of nw takes
+// rows w, w + nw, ...  Per row the lanes walk its (equation, column) values with the
+// column fastest (column index len is the RHS entry), so each equation's segment is
+// stored contiguously.  The warp reads 32 flush records at a time, one per lane.
+__device__ __forceinline__ void flush_rows(const RoArgs& r, float* win, int tb, int w0, int nw) {
   const AsmArgs<float>& A_ = r.a;
   const int lane = threadIdx.x & 31, n_eq = A_.eq_count;
-  for (int f = r.batch_flush[tb] + (threadIdx.x >> 5); f < r.batch_flush[tb + 1]; f += THREADS / 32) {
-    const int32_t row = r.flush_row[f];
-    const int base = r.flush_slot[f] * r.row_stride;
-    const int64_t k0 = A_.rowptr[row];
-    const int len = (int)(A_.rowptr[row + 1] - k0);
+  const int f0 = r.batch_flush[tb], nf = r.batch_flush[tb + 1] - f0;
+  int4 rec = make_int4(0, 0, 0, 0);
+  for (int f = w0, j = 32; f < nf; f += nw, ++j) {
+    if (j == 32) {  // records f, f + nw, ..., f + 31 nw
+      const int fl = f + lane * nw;
+      if (fl < nf) rec = __ldg(r.flush_meta + f0 + fl);
+      j = 0;
+    }
+    const int4 m = make_int4(__shfl_sync(0xffffffffu, rec.x, j), __shfl_sync(0xffffffffu, rec.y, j),
+                             __shfl_sync(0xffffffffu, rec.z, j), __shfl_sync(0xffffffffu, rec.w, j));
+    const int32_t row = m.x, base = m.y, len = m.w;
+    const int64_t k0 = (int64_t)(uint32_t)m.z;
     const int w = len + 1;
     int q = lane / w, c = lane - q * w;  // position of this lane, advanced by 32 values per step
     const int step_q = 32 / w, step_c = 32 - step_q * w;
-    // separate loops: with the accumulate test inside, the compiler may read *dst unconditionally
-    if (!r.accumulate) {
+    if (w <= 32 && !r.accumulate) {
+      // Rows of at most 31 columns: lane = column (lane len = RHS entry), so each store
+      // instruction writes one contiguous row segment of one equation; eight equations'
+      // values are read from shared memory before their eight stores are issued.
+      if (lane < w) {
+        const float* src = win + (base + (lane < len ? lane : r.maxcol)) * r.neqs;
+        float* dv = A_.values + (int64_t)A_.eq0 * A_.nnz + k0 + lane;
+        float* dr = A_.rhs + (int64_t)A_.eq0 * A_.n_node + row;
+        for (int q0 = 0; q0 < n_eq; q0 += 8) {
+          float v[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] = q0 + k < n_eq ? src[q0 + k] : 0.f;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            if (q0 + k >= n_eq) break;
+            if (lane < len) __stcs(dv + (int64_t)(q0 + k) * A_.nnz, v[k]);
+            else __stcs(dr + (int64_t)(q0 + k) * A_.n_node, v[k]);
+          }
+        }
+      }
+    } else if (!r.accumulate) {
 #pragma unroll 4
       for (int idx = lane; idx < w * n_eq; idx += 32) {
         const float v = win[(base + (c < len ? c : r.maxcol)) * r.neqs + q];
@@ -288,7 +323,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
     if (u >= r.n_units) break;
     const int t0 = r.unit_batch[2 * u], t1 = r.unit_batch[2 * u + 1];
     // prologue: batch t0 into buffer 0, plan data of t0+1 into buffer 1
-    __syncthreads();
     stage_plan(r, t0, stage(0));
     cp_async_commit();
     cp_async_wait_all();
@@ -303,6 +337,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
       const int nv = r.batch_visit[t + 1] - r.batch_visit[t];
       const int items = nv * n_eq;
       cp_async_wait_all();  // raw node data of t, plan data of t+1
+      // batch t's data has landed; batch t-1 is computed and the rows of t-2 are written
       __syncthreads();
       if (t + 1 < t1) stage_nodes(r, t + 1, Sn);
       cp_async_commit();
@@ -312,18 +347,15 @@ __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
       __syncthreads();
       float kn[NEN], sn[NEN], pn[NEN];
       if (tid < items) load_fields(r, S, tid / n_eq, tid % n_eq, kn, sn, pn);
-      // element matrices: items tid, tid + THREADS (element = item / n_eq, equation = item % n_eq)
-      for (int item = tid; item < items; item += THREADS) {
-        const int el = item / n_eq, q = item - el * n_eq;
-        const float* Ge = geo + el * GEO_ELEM;
-        const float ck = Ge[NG * GEO];
+      // element matrices: items tid, tid + THREADS, ... (element = item / n_eq, equation = item % n_eq)
+      const int rounds = max(1, (items + THREADS - 1) / THREADS);
+      const int flush_at = rounds >= 2 ? 1 : 0;  // the same for every thread
+      for (int it = 0; it < rounds; ++it) {
+        if (it == flush_at && t > t0) flush_rows(r, win, t - 1, warp, THREADS / 32);
+        const int item = tid + it * THREADS;
+        const bool has = item < items;  // threads without an item still meet every barrier
+        const int el = has ? item / n_eq : 0, q = has ? item - el * n_eq : 0;
         const uint32_t* eo = reinterpret_cast<const uint32_t*>(S.off + el * OFFS);
-        float kg[NG], sg[NG], pg[NG];
-        interp8(kn, kg);
-        interp8(sn, sg);
-        interp8(pn, pg);
-        if (item + THREADS < items)  // prefetch the next item's fields while this one computes
-          load_fields(r, S, (item + THREADS) / n_eq, (item + THREADS) % n_eq, kn, sn, pn);
         float2 Am[NEN][NEN / 2], Dm[18], bv2[NEN / 2];
 #pragma unroll
         for (int a = 0; a < NEN; ++a)
@@ -333,114 +365,132 @@ __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
         for (int k2 = 0; k2 < 18; ++k2) Dm[k2] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int a = 0; a < NEN / 2; ++a) bv2[a] = make_float2(0.f, 0.f);
+        if (has) {
+          const float* Ge = geo + el * GEO_ELEM;
+          const float ck = Ge[NG * GEO];
+          float kg[NG], sg[NG], pg[NG];
+          interp8(kn, kg);
+          interp8(sn, sg);
+          interp8(pn, pg);
+          if (item + THREADS < items)  // prefetch the next item's fields while this one computes
+            load_fields(r, S, (item + THREADS) / n_eq, (item + THREADS) % n_eq, kn, sn, pn);
 #pragma unroll
-        for (int g = 0; g < NG; ++g) {
-          const float4* G4 = reinterpret_cast<const float4*>(Ge + g * GEO);
-          float gv[GEO];
+          for (int g = 0; g < NG; ++g) {
+            const float4* G4 = reinterpret_cast<const float4*>(Ge + g * GEO);
+            float gv[GEO];
 #pragma unroll
-          for (int k2 = 0; k2 < GEO / 4 - 1; ++k2) {
-            const float4 x = G4[k2];
-            gv[4 * k2] = x.x;
-            gv[4 * k2 + 1] = x.y;
-            gv[4 * k2 + 2] = x.z;
-            gv[4 * k2 + 3] = x.w;
-          }
-          {
-            const float4 x = G4[GEO / 4 - 1];
-            gv[GEO - 4] = x.x;
-            gv[GEO - 3] = x.y;
-          }
-          const float dv = gv[0];
-          const float den = fmaf(ck, kg[g], gv[1] + sg[g]);
-          const float tau = den > 0.f ? __fdividef(1.f, den) : 0.f;
-          const float dvt = t_supg ? dv * tau : 0.f;
-          const float sigs = inv_dt + sg[g];
-          float P[NEN], Q[NEN];
-          if (FULL) {
-            // all terms: dV (N_a + tau u.gradN_a)((1/dt + s) N_b + u.gradN_b), one rank-1 product
-#pragma unroll
-            for (int a = 0; a < NEN; ++a) {
-              P[a] = fmaf(dvt, gv[2 + a], dv * hex_n(a, g));
-              Q[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
+            for (int k2 = 0; k2 < GEO / 4 - 1; ++k2) {
+              const float4 x = G4[k2];
+              gv[4 * k2] = x.x;
+              gv[4 * k2 + 1] = x.y;
+              gv[4 * k2 + 2] = x.z;
+              gv[4 * k2 + 3] = x.w;
             }
-#pragma unroll
-            for (int a = 0; a < NEN; ++a) {
-              const float2 pa = make_float2(P[a], P[a]);
-#pragma unroll
-              for (int b = 0; b < NEN / 2; ++b) Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
+            {
+              const float4 x = G4[GEO / 4 - 1];
+              gv[GEO - 4] = x.x;
+              gv[GEO - 3] = x.y;
             }
-          } else {
-            // dV N_a (sig N_b + [conv] u.gradN_b) + [supg] dV tau u.gradN_a ((1/dt + s) N_b + u.gradN_b)
-            const float sig = (t_mass ? inv_dt : 0.f) + (t_reac ? sg[g] : 0.f);
-            float Ps[NEN], R[NEN];
+            const float dv = gv[0];
+            const float den = fmaf(ck, kg[g], gv[1] + sg[g]);
+            const float tau = den > 0.f ? __fdividef(1.f, den) : 0.f;
+            const float dvt = t_supg ? dv * tau : 0.f;
+            const float sigs = inv_dt + sg[g];
+            float P[NEN], Q[NEN];
+            if (FULL) {
+              // all terms: dV (N_a + tau u.gradN_a)((1/dt + s) N_b + u.gradN_b), one rank-1 product
 #pragma unroll
-            for (int a = 0; a < NEN; ++a) {
-              P[a] = dv * hex_n(a, g);
-              Ps[a] = dvt * gv[2 + a];
-              Q[a] = sig * hex_n(a, g) + (t_conv ? gv[2 + a] : 0.f);
-              R[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
-            }
-#pragma unroll
-            for (int a = 0; a < NEN; ++a) {
-              const float2 pa = make_float2(P[a], P[a]), ps = make_float2(Ps[a], Ps[a]);
-#pragma unroll
-              for (int b = 0; b < NEN / 2; ++b) {
-                Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
-                Am[a][b] = __ffma2_rn(ps, make_float2(R[2 * b], R[2 * b + 1]), Am[a][b]);
+              for (int a = 0; a < NEN; ++a) {
+                P[a] = fmaf(dvt, gv[2 + a], dv * hex_n(a, g));
+                Q[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
               }
+#pragma unroll
+              for (int a = 0; a < NEN; ++a) {
+                const float2 pa = make_float2(P[a], P[a]);
+#pragma unroll
+                for (int b = 0; b < NEN / 2; ++b) Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
+              }
+            } else {
+              // dV N_a (sig N_b + [conv] u.gradN_b) + [supg] dV tau u.gradN_a ((1/dt + s) N_b + u.gradN_b)
+              const float sig = (t_mass ? inv_dt : 0.f) + (t_reac ? sg[g] : 0.f);
+              float Ps[NEN], R[NEN];
+#pragma unroll
+              for (int a = 0; a < NEN; ++a) {
+                P[a] = dv * hex_n(a, g);
+                Ps[a] = dvt * gv[2 + a];
+                Q[a] = sig * hex_n(a, g) + (t_conv ? gv[2 + a] : 0.f);
+                R[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
+              }
+#pragma unroll
+              for (int a = 0; a < NEN; ++a) {
+                const float2 pa = make_float2(P[a], P[a]), ps = make_float2(Ps[a], Ps[a]);
+#pragma unroll
+                for (int b = 0; b < NEN / 2; ++b) {
+                  Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
+                  Am[a][b] = __ffma2_rn(ps, make_float2(R[2 * b], R[2 * b + 1]), Am[a][b]);
+                }
+              }
+              if (!t_mass) {
+#pragma unroll
+                for (int a = 0; a < NEN; ++a) P[a] = 0.f;
+              }
+#pragma unroll
+              for (int a = 0; a < NEN; ++a) P[a] += Ps[a];
             }
-            if (!t_mass) {
+            if (t_diff) {
+              const float2 k2v = make_float2(kg[g], kg[g]);
 #pragma unroll
-              for (int a = 0; a < NEN; ++a) P[a] = 0.f;
+              for (int k2 = 0; k2 < 18; ++k2) Dm[k2] = __ffma2_rn(k2v, make_float2(gv[10 + 2 * k2], gv[11 + 2 * k2]), Dm[k2]);
             }
+            const float2 pdt = make_float2(pg[g] * inv_dt, pg[g] * inv_dt);
 #pragma unroll
-            for (int a = 0; a < NEN; ++a) P[a] += Ps[a];
+            for (int a = 0; a < NEN / 2; ++a) bv2[a] = __ffma2_rn(make_float2(P[2 * a], P[2 * a + 1]), pdt, bv2[a]);
           }
-          if (t_diff) {
-            const float2 k2v = make_float2(kg[g], kg[g]);
+        }  // has
+        // add into the shared-memory rows (offsets are in row-window entries of neqs floats):
+        // local rows a and a + 4 in round a & 3.  The plan lets two elements of a batch share
+        // an owned node only in different rounds, so no two threads touch the same word
+        // between two barriers.  Per matrix row the 9 words (8 columns and the RHS) are
+        // distinct, so all 9 are loaded before any is stored (the compiler cannot prove that
+        // and would otherwise serialise every load behind the previous store).
 #pragma unroll
-            for (int k2 = 0; k2 < 18; ++k2) Dm[k2] = __ffma2_rn(k2v, make_float2(gv[10 + 2 * k2], gv[11 + 2 * k2]), Dm[k2]);
+        for (int rho = 0; rho < ROUNDS; ++rho) {
+#pragma unroll
+          for (int a = rho; a < NEN; a += ROUNDS) {
+            if (!has) break;
+            const uint32_t rw = eo[(NEN * NEN + a) / 2];
+            const uint32_t ro = (a & 1) ? (rw >> 16) : (rw & 0xFFFFu);
+            if (ro == NONE) continue;
+            float* p[NEN + 1];
+            float add[NEN + 1];
+#pragma unroll
+            for (int b = 0; b < NEN; b += 2) {
+              const uint32_t w2 = eo[(a * NEN + b) / 2];
+              const int i0 = a <= b ? sym_index(a, b) : sym_index(b, a);
+              const int i1 = a <= b + 1 ? sym_index(a, b + 1) : sym_index(b + 1, a);
+              p[b] = win + (int)(w2 & 0xFFFFu) * r.neqs + q;
+              p[b + 1] = win + (int)(w2 >> 16) * r.neqs + q;
+              add[b] = Am[a][b / 2].x + ((i0 & 1) ? Dm[i0 >> 1].y : Dm[i0 >> 1].x);
+              add[b + 1] = Am[a][b / 2].y + ((i1 & 1) ? Dm[i1 >> 1].y : Dm[i1 >> 1].x);
+            }
+            p[NEN] = win + (int)ro * r.neqs + q;
+            add[NEN] = (a & 1) ? bv2[a / 2].y : bv2[a / 2].x;
+            float old[NEN + 1];
+#pragma unroll
+            for (int b = 0; b <= NEN; ++b) old[b] = *p[b];
+#pragma unroll
+            for (int b = 0; b <= NEN; ++b) *p[b] = old[b] + add[b];
           }
-          const float2 pdt = make_float2(pg[g] * inv_dt, pg[g] * inv_dt);
-#pragma unroll
-          for (int a = 0; a < NEN / 2; ++a) bv2[a] = __ffma2_rn(make_float2(P[2 * a], P[2 * a + 1]), pdt, bv2[a]);
-        }
-        // add into the shared-memory rows (offsets are in row-window entries of neqs floats).
-        // The elements of a batch share no owned node, so no two threads touch the same word.
-        // Per matrix row: the 9 words (8 columns and the RHS) are distinct, so all 9 are
-        // loaded before any is stored (the compiler cannot prove that and would otherwise
-        // serialise every load behind the previous store).
-#pragma unroll
-        for (int a = 0; a < NEN; ++a) {
-          const uint32_t rw = eo[(NEN * NEN + a) / 2];
-          const uint32_t ro = (a & 1) ? (rw >> 16) : (rw & 0xFFFFu);
-          if (ro == NONE) continue;
-          float* p[NEN + 1];
-          float add[NEN + 1];
-#pragma unroll
-          for (int b = 0; b < NEN; b += 2) {
-            const uint32_t w2 = eo[(a * NEN + b) / 2];
-            const int i0 = a <= b ? sym_index(a, b) : sym_index(b, a);
-            const int i1 = a <= b + 1 ? sym_index(a, b + 1) : sym_index(b + 1, a);
-            p[b] = win + (int)(w2 & 0xFFFFu) * r.neqs + q;
-            p[b + 1] = win + (int)(w2 >> 16) * r.neqs + q;
-            add[b] = Am[a][b / 2].x + ((i0 & 1) ? Dm[i0 >> 1].y : Dm[i0 >> 1].x);
-            add[b + 1] = Am[a][b / 2].y + ((i1 & 1) ? Dm[i1 >> 1].y : Dm[i1 >> 1].x);
-          }
-          p[NEN] = win + (int)ro * r.neqs + q;
-          add[NEN] = (a & 1) ? bv2[a / 2].y : bv2[a / 2].x;
-          float old[NEN + 1];
-#pragma unroll
-          for (int b = 0; b <= NEN; ++b) old[b] = *p[b];
-#pragma unroll
-          for (int b = 0; b <= NEN; ++b) *p[b] = old[b] + add[b];
+          __syncthreads();
         }
       }
-      __syncthreads();
-      // rows completed by batch t; plan data of t+2 into the buffer that batch t used
-      flush_rows(r, win, t);
+      // the last round's barrier: every thread is done with the plan data in S
       if (t + 2 < t1) stage_plan(r, t + 2, S);
       cp_async_commit();
     }
+    // the rows the last batch completed, by all warps
+    __syncthreads();
+    flush_rows(r, win, t1 - 1, warp, THREADS / 32);
+    __syncthreads();
   }
 }
