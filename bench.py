@@ -207,7 +207,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--scatter", type=int, default=0, help="0 auto, 1 atomic, 2 row-owned")
+    ap.add_argument("--scatter", type=int, default=0, help="0 auto, 1 atomic, 2 row-owned, 3 gather")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f64", action="store_true")

@@ -86,7 +86,10 @@ enum {
 typedef enum {
   FEA_SCATTER_AUTO = 0,     /* pick per element type and size (autotuned) */
   FEA_SCATTER_ATOMIC = 1,   /* element-parallel, atomic adds into zeroed outputs */
-  FEA_SCATTER_ROWOWNED = 2  /* rows accumulated in shared memory and written once (deterministic) */
+  FEA_SCATTER_ROWOWNED = 2, /* rows accumulated in shared memory and written once (deterministic) */
+  FEA_SCATTER_GATHER = 3    /* FP32 only: element matrices to a device scratch buffer owned by the pattern,
+                               then every CSR row summed by one warp over its incident elements in
+                               ascending element order and written once (deterministic) */
 } fea_scatter;
 
 typedef struct {

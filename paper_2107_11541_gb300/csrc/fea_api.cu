@@ -310,6 +310,15 @@ k_rows(const int32_t* __restrict__ conn, int nen, const int64_t* __restrict__ in
   }
 }
 
+// Longest row: max of the row counts, into *out (zeroed by the caller).
+__global__ void k_maxlen(const int32_t* __restrict__ rowcnt, int64_t n, int32_t* out) {
+  int32_t m = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, rowcnt[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 __global__ void k_posmap(const int32_t* __restrict__ conn, int64_t n_elem, int nen, const int64_t* __restrict__ rowptr,
                          const int32_t* __restrict__ colind, int32_t* pos) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,7 +355,9 @@ static fea_status check_assemble_args(fea_mesh* m, const fea_pattern* p, const v
   if (!vel || !kd || !sr || !phi || !values || !rhs) return fail(FEA_ERR_ARG, "a field or output pointer is null");
   if (o->precision != FEA_F64_PLAIN && o->precision != FEA_F32_FUSED) return fail(FEA_ERR_ARG, "unknown precision");
   if (o->terms & ~FEA_TERM_ALL) return fail(FEA_ERR_ARG, "unknown term bits");
-  if (o->scatter < FEA_SCATTER_AUTO || o->scatter > FEA_SCATTER_ROWOWNED) return fail(FEA_ERR_ARG, "unknown scatter");
+  if (o->scatter < FEA_SCATTER_AUTO || o->scatter > FEA_SCATTER_GATHER) return fail(FEA_ERR_ARG, "unknown scatter");
+  if (o->scatter == FEA_SCATTER_GATHER && o->precision != FEA_F32_FUSED)
+    return fail(FEA_ERR_ARG, "the gather scatter is an FP32 path");
   return FEA_OK;
 }
 
@@ -368,6 +379,9 @@ static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, 
   a.phi = (const T*)phi;
   a.values = (T*)values;
   a.rhs = (T*)rhs;
+  a.em = nullptr;
+  a.inc_ptr = p->inc_ptr;
+  a.inc_elem = p->inc_elem;
   a.n_node = m->n_node;
   a.n_elem = m->n_elem;
   a.nnz = p->nnz;
@@ -501,6 +515,7 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->inc_ptr);
   cudaFree(p->inc_elem);
   cudaFree(p->ws);
+  cudaFree(p->em);
   plan_destroy(p->plan);
   delete p;
   return FEA_OK;
@@ -553,12 +568,20 @@ fea_status fea_pattern_build(fea_mesh* m, fea_pattern** out) {
   st = exclusive_scan(rowcnt, N, p->rowptr, s);
   if (st != FEA_OK) return done(st);
   int64_t nnz = 0;
+  int32_t maxcol = 0;
   if (cudaMemcpyAsync(&nnz, p->rowptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return done(fail(FEA_ERR_CUDA, "nnz readback failed"));
+  if (N > 0) {  // longest row, into cnt[0] (the incidence counters are no longer needed)
+    cudaMemsetAsync(cnt, 0, sizeof(int32_t), s);
+    k_maxlen<<<(unsigned)std::min<int64_t>(grid_for(N, 256), 152 * 8), 256, 0, s>>>(rowcnt, N, cnt);
+    if (cudaMemcpyAsync(&maxcol, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return done(fail(FEA_ERR_CUDA, "row length readback failed"));
+  }
   st = fea_sync(m);
   if (st != FEA_OK) return done(st);
   if (nnz >= (int64_t)INT32_MAX) return done(fail(FEA_ERR_TOO_LARGE, "nnz %lld >= 2^31", (long long)nnz));
   p->nnz = nnz;
+  p->maxcol = maxcol;
   if (cudaMalloc(&p->colind, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
       cudaMalloc(&p->pos, sizeof(int32_t) * std::max<int64_t>(tot * nen, 1)) != cudaSuccess) {
     cudaGetLastError();
@@ -587,11 +610,27 @@ fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, cons
   cudaStream_t s = m->stream;
   size_t es = o.precision == FEA_F64_PLAIN ? sizeof(double) : sizeof(float);
   bool rowowned = false;
-  if (o.precision == FEA_F32_FUSED && o.scatter != FEA_SCATTER_ATOMIC)
+  if (o.precision == FEA_F32_FUSED && (o.scatter == FEA_SCATTER_AUTO || o.scatter == FEA_SCATTER_ROWOWNED))
     FEA_TRY(plan_prepare(p->plan, n_eq, &rowowned));
   if (o.scatter == FEA_SCATTER_ROWOWNED && !rowowned)
     return fail(FEA_ERR_ARG, "row-owned scatter is not available for this mesh type, precision or equation count");
-  if (!o.accumulate && !rowowned) {
+  const bool gather = o.scatter == FEA_SCATTER_GATHER;
+  if (gather && m->n_elem > 0) {
+    fea_pattern* pw = const_cast<fea_pattern*>(p);  // the scratch belongs to the pattern
+    const size_t need = gather_scratch_bytes(m->n_elem, m->nen, n_eq);
+    if (pw->em_bytes < need) {
+      FEA_CUDA_TRY(cudaStreamSynchronize(s));  // the old scratch may still be in use on the stream
+      cudaFree(pw->em);
+      pw->em = nullptr;
+      pw->em_bytes = 0;
+      if (cudaMalloc(&pw->em, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FEA_ERR_OOM, "gather scatter: %zu bytes of element-matrix scratch", need);
+      }
+      pw->em_bytes = need;
+    }
+  }
+  if (!o.accumulate && !rowowned && !(gather && m->n_elem > 0)) {
     FEA_CUDA_TRY(cudaMemsetAsync(values, 0, es * (size_t)n_eq * (size_t)p->nnz, s));
     FEA_CUDA_TRY(cudaMemsetAsync(rhs, 0, es * (size_t)n_eq * (size_t)m->n_node, s));
   }
@@ -606,8 +645,15 @@ fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, cons
       }
     } else {
       AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
-      if (rowowned) FEA_TRY(plan_assemble(p->plan, a, o.accumulate, s));
-      else FEA_TRY(launch_generic_f32(a, m->type, s));
+      if (rowowned) {
+        FEA_TRY(plan_assemble(p->plan, a, o.accumulate, s));
+      } else if (gather) {
+        a.em = (float*)p->em;
+        FEA_TRY(launch_generic_f32(a, m->type, s));
+        FEA_TRY(launch_gather_f32(a, m->type, p->maxcol, o.accumulate != 0, s));
+      } else {
+        FEA_TRY(launch_generic_f32(a, m->type, s));
+      }
     }
   }
   if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, s));

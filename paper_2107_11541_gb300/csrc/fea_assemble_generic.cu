@@ -5,7 +5,9 @@
 // once per element; then, per equation, the per-point coefficients (k, s, phi,
 // tau) and the NEN x NEN element matrix (Sec. 4.2, Listing 1, generalised to the
 // full Galerkin + SUPG operator) are formed with entries spread over the lanes,
-// and scatter-added with atomics into the zeroed CSR values and RHS.
+// and scatter-added with atomics into the zeroed CSR values and RHS -- or, for the
+// gather scatter, stored to the element-matrix scratch [e][entry][equation]
+// (entries a*NEN+b, then NEN*NEN+a for the RHS) for the row gather.
 //
 // Used as (a) the plain FP64 path: one launch per equation (eq_count = 1), the
 // geometry recomputed every launch; and (b) the portable FP32 fused path: one
@@ -64,6 +66,7 @@ template <typename T, int TYPE, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_generic(AsmArgs<T> p) {
   using L = GenericSmem<T, TYPE>;
   constexpr int NEN = L::NEN, NG = L::NG, ORDER = Elem<TYPE>::ORDER;
+  constexpr int64_t EM_ENTRIES = NEN * NEN + NEN;
   extern __shared__ __align__(16) unsigned char sm_generic[];
   T* Nt = reinterpret_cast<T*>(sm_generic);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -184,7 +187,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_generic(AsmArgs<T> p) {
           if (t_supg) t += S[L::TAU + g] * uaa * (Nb * inv_dt + uab + sg * Nb);
           acc += S[L::DV + g] * t;
         }
-        atomic_add(vq + pe[idx], acc);
+        if (p.em) p.em[((e * EM_ENTRIES) + idx) * p.eq_count + (q - p.eq0)] = acc;
+        else atomic_add(vq + pe[idx], acc);
       }
       for (int a = lane; a < NEN; a += 32) {
         T acc = T(0);
@@ -194,7 +198,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_generic(AsmArgs<T> p) {
           if (t_supg) test += S[L::TAU + g] * S[L::UA + g * NEN + a];
           acc += S[L::DV + g] * test * S[L::PG + g] * inv_dt;
         }
-        atomic_add(p.rhs + fo + node[a], acc);
+        if (p.em) p.em[((e * EM_ENTRIES) + NEN * NEN + a) * p.eq_count + (q - p.eq0)] = acc;
+        else atomic_add(p.rhs + fo + node[a], acc);
       }
       __syncwarp();
     }

@@ -77,6 +77,10 @@ struct fea_pattern {
   int64_t* inc_ptr;    // [n_node+1] node -> element incidence
   int32_t* inc_elem;   // [nen*n_elem]
   fea_rowowned_plan* plan;  // may be null (row-owned path unavailable for this mesh)
+  int32_t maxcol;      // longest row
+  // element-matrix scratch of the gather scatter, grown on demand
+  void* em;
+  size_t em_bytes;
   // device workspace for fea_assemble_host
   void* ws;
   size_t ws_bytes;
@@ -211,6 +215,10 @@ struct AsmArgs {
   const T* phi;    // [n_eq][N]
   T* values;       // [n_eq][nnz]
   T* rhs;          // [n_eq][N]
+  T* em;           // gather scatter: [n_elem][nen*nen + nen][eq_count] element matrices and RHS
+                   // (written instead of the atomic adds); null otherwise
+  const int64_t* inc_ptr;   // [n_node+1] node -> incident elements
+  const int32_t* inc_elem;  // ascending element ids per node
   int64_t n_node;
   int64_t n_elem;
   int64_t nnz;
@@ -226,5 +234,9 @@ struct AsmArgs {
 // Launchers (defined in the kernel translation units).
 fea_status launch_generic_f64(const AsmArgs<double>& a, fea_elem_t type, cudaStream_t s);
 fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s);
+// Row gather of the element matrices in a.em into a.values / a.rhs (overwrite or add).
+fea_status launch_gather_f32(const AsmArgs<float>& a, fea_elem_t type, int maxcol, bool accumulate, cudaStream_t s);
+// Bytes of element-matrix scratch the gather scatter needs.
+size_t gather_scratch_bytes(int64_t n_elem, int nen, int n_eq);
 
 }  // namespace fea

@@ -51,7 +51,7 @@ def test_f64_plain_parity(case):
     assert ea <= TOL_F64 and eb <= TOL_F64, (ea, eb)
 
 
-@pytest.mark.parametrize("scatter", [fea.FEA_SCATTER_AUTO, fea.FEA_SCATTER_ATOMIC])
+@pytest.mark.parametrize("scatter", [fea.FEA_SCATTER_AUTO, fea.FEA_SCATTER_ATOMIC, fea.FEA_SCATTER_GATHER])
 def test_f32_fused_parity(case, scatter):
     w, run = case
     v, r = run.assemble(w.fields, fea.FEA_F32_FUSED, scatter=scatter)
@@ -77,7 +77,7 @@ def test_accumulate_adds(case):
     v2, r2 = run.assemble(w.fields, fea.FEA_F64_PLAIN, accumulate=1, out=(v1.clone(), r1.clone()))
     assert np.allclose(v2.cpu().numpy(), 2 * v1.cpu().numpy(), rtol=1e-13, atol=0)
     assert np.allclose(r2.cpu().numpy(), 2 * r1.cpu().numpy(), rtol=1e-13, atol=0)
-    for scatter in (fea.FEA_SCATTER_AUTO, fea.FEA_SCATTER_ATOMIC):
+    for scatter in (fea.FEA_SCATTER_AUTO, fea.FEA_SCATTER_ATOMIC, fea.FEA_SCATTER_GATHER):
         v1, r1 = run.assemble(w.fields, fea.FEA_F32_FUSED, scatter=scatter)
         v2, r2 = run.assemble(w.fields, fea.FEA_F32_FUSED, scatter=scatter, accumulate=1,
                               out=(v1.clone(), r1.clone()))
@@ -113,8 +113,10 @@ def test_unused_nodes_and_subset():
         orp, oci, opos = O.pattern(mesh.elem_type, mesh.conn, mesh.n_node)
         assert np.array_equal(rp, orp) and np.array_equal(ci, oci) and np.array_equal(pos, opos)
         assert (np.diff(rp) == 0).any()
-        for prec, tol in ((fea.FEA_F64_PLAIN, TOL_F64), (fea.FEA_F32_FUSED, TOL_F32)):
-            v, r = run.assemble(fields, prec)
+        for prec, tol, scatter in ((fea.FEA_F64_PLAIN, TOL_F64, fea.FEA_SCATTER_AUTO),
+                                   (fea.FEA_F32_FUSED, TOL_F32, fea.FEA_SCATTER_AUTO),
+                                   (fea.FEA_F32_FUSED, TOL_F32, fea.FEA_SCATTER_GATHER)):
+            v, r = run.assemble(fields, prec, scatter=scatter)
             ea, eb = compare_full(run, fields, prec, values=v, rhs=r)
             assert ea <= tol and eb <= tol
     finally:
@@ -160,16 +162,23 @@ def test_bad_arguments(case):
         with pytest.raises(fea.FeaError) as e:
             fea.fea_assemble(run.handle, run.pattern, vel, kd, sr, phi, args[1], args[0], opts, vals, rhs)
         assert e.value.code == code
+    for bad in (dict(scatter=7), dict(scatter=fea.FEA_SCATTER_GATHER, precision=fea.FEA_F64_PLAIN)):
+        with pytest.raises(fea.FeaError) as e:
+            fea.fea_assemble(run.handle, run.pattern, vel, kd, sr, phi, 1e-3, 1, fea.fea_default_opts(**bad), vals,
+                             rhs)
+        assert e.value.code == 1, bad
 
 
-def test_deterministic_rowowned_is_bitwise_stable(case):
-    """The row-owned scatter (where available) gives the same bits on every run."""
+@pytest.mark.parametrize("scatter", [fea.FEA_SCATTER_ROWOWNED, fea.FEA_SCATTER_GATHER])
+def test_deterministic_scatter_is_bitwise_stable(case, scatter):
+    """The deterministic scatters (row-owned where available, gather everywhere) give the
+    same bits on every run."""
     w, run = case
     try:
-        v1, r1 = run.assemble(w.fields, fea.FEA_F32_FUSED, scatter=fea.FEA_SCATTER_ROWOWNED)
+        v1, r1 = run.assemble(w.fields, fea.FEA_F32_FUSED, scatter=scatter)
     except fea.FeaError:
         pytest.skip("row-owned scatter not available for this element type")
-    v2, r2 = run.assemble(w.fields, fea.FEA_F32_FUSED, scatter=fea.FEA_SCATTER_ROWOWNED)
+    v2, r2 = run.assemble(w.fields, fea.FEA_F32_FUSED, scatter=scatter)
     assert np.array_equal(v1.cpu().numpy(), v2.cpu().numpy())
     assert np.array_equal(r1.cpu().numpy(), r2.cpu().numpy())
     ea, eb = compare_full(run, w.fields, fea.FEA_F32_FUSED, values=v1, rhs=r1)
