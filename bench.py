@@ -193,6 +193,20 @@ def run_reference(args, w, rank):
     print(json.dumps(out), flush=True)
 
 
+def field_update_parity(mesh, phi0, phi_gpu, prm, seq):
+    """Max |phi_gpu - oracle| on 4096 sampled nodes after the bench's field updates, applied
+    with the parameter rows ``seq`` in order (warm-up steps, the update timed outside the
+    graph, then the graph's steps)."""
+    import oracle as O
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(mesh.n_node, size=min(4096, mesh.n_node), replace=False))
+    phi = phi0[:, idx].astype(np.float64)
+    for s in seq:
+        phi = O.update_fields(mesh.coords[idx], phi, prm[s].astype(np.float64))
+    err = float(np.abs(phi_gpu[:, idx] - phi).max())
+    return {"nodes": int(idx.size), "updates": len(seq), "max_abs_err": err, "tol": 1e-5, "pass": err <= 1e-5}
+
+
 def config_dict(workload, w, nnz):
     m = w.mesh
     return {"workload": workload, "elem_type": G.NAMES[m.elem_type], "elements": m.n_elem, "nodes": m.n_node,
@@ -214,7 +228,12 @@ def main():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cells", type=int, default=None, help="shrink to this many cells per axis (profiling)")
+    ap.add_argument("--graph", type=int, default=None,
+                    help="1: time the K steps as one CUDA graph of K (assemble, field update) time steps "
+                         "(default on for hex8_256_32eq)")
     args = ap.parse_args()
+    if args.graph is None:
+        args.graph = 1 if args.workload == "hex8_256_32eq" else 0
     rank, world, local = dist_env()
     w = make(args.workload, args.cells)
     if args.impl == "reference":
@@ -251,13 +270,34 @@ def main():
             opts.event_begin = opts.event_end = None
         fea.fea_assemble(h, p, *dev, fld.dt, q, opts, values, rhs)
 
-    for _ in range(args.warmup):
-        step()
+    graph = None
+    if args.graph:
+        # time steps: assemble, then the seeded field perturbation, K of them in one CUDA graph
+        prm = torch.from_numpy(G.step_params(max(args.steps, args.warmup), q)).cuda()
+        for s in range(args.warmup):
+            step()
+            fea.fea_update_fields(h, dev[3], q, prm[s])
+    else:
+        for _ in range(args.warmup):
+            step()
     fea.fea_sync(h)
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    n_kev = 1 if args.graph else args.steps
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_kev)]
     for a, b in kev:  # torch creates the CUDA events lazily, on first record
         a.record(stream)
         b.record(stream)
+    update_ms = None
+    if args.graph:
+        # kernel times outside the graph: one assembly and one field update, each between events
+        step(kev[0])
+        ua, ub = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ua.record(stream)
+        fea.fea_update_fields(h, dev[3], q, prm[0])
+        ub.record(stream)
+        torch.cuda.synchronize()
+        update_ms = ua.elapsed_time(ub)
+        opts.event_begin = opts.event_end = None
+        graph = fea.fea_graph_capture_steps(h, p, *dev, fld.dt, q, opts, values, rhs, prm, args.steps)
     t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     if dist is not None:
@@ -267,15 +307,20 @@ def main():
     clocks.start()
     time.sleep(0.3)
     t0e.record(stream)
-    for s in range(args.steps):
-        step(kev[s])
+    if graph is not None:
+        fea.fea_graph_launch(graph)
+    else:
+        for s in range(args.steps):
+            step(kev[s])
     t1e.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = fea.fea_kernel_launches() - launches0
     fea.fea_sync(h)
+    if graph is not None:
+        fea.fea_graph_destroy(graph)
     ms = t0e.elapsed_time(t1e) / args.steps
-    kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
+    kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
     if dist is not None:
         t = torch.tensor([ms, kernel_ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -306,6 +351,20 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args.workload, w, nnz),
            "clocks": clk, "gpu_launches": int(launches), "kernel_ms": kernel_ms, "roofline": roof,
            "roofline_other": other}
+    if args.graph:
+        out["graph"] = {"time_steps": args.steps, "launches": 1, "step": "assemble, then field update",
+                        "update_ms": update_ms, "assemble_ms": kernel_ms}
+        if rank == 0 and not args.no_parity:
+            # the graph's last assembly used the field before the last update; check an eager assembly of
+            # the current field instead (same code), and the updated field on sampled nodes
+            fea.fea_assemble(h, p, *dev, fld.dt, q, opts, values, rhs)
+            fea.fea_sync(h)
+            fld = G.Fields(fld.velocity, fld.diffusivity, fld.reaction,
+                           dev[3].cpu().numpy().astype(np.float64), fld.dt)
+            w = G.Workload(w.name, w.mesh, fld, w.precision)
+            seq = list(range(args.warmup)) + [0] + list(range(args.steps))
+            out["field_update_parity"] = field_update_parity(w.mesh, f32.phi_old, fld.phi_old,
+                                                             G.step_params(max(args.steps, args.warmup), q), seq)
 
     if rank == 0 and not args.no_parity:
         out["parity"] = sampled_parity(w, values, rhs, p, nnz)

@@ -53,6 +53,7 @@ extern "C" {
 
 typedef struct fea_mesh fea_mesh;
 typedef struct fea_pattern fea_pattern;
+typedef struct fea_graph fea_graph;
 
 typedef enum { FEA_TET4 = 0, FEA_HEX8 = 1, FEA_HEX27 = 2 } fea_elem_t;
 
@@ -196,6 +197,39 @@ FEA_API fea_status fea_pack_plan(const int64_t* count_by_type, int32_t n_types, 
  * make that first call before any stream capture.
  */
 FEA_API fea_status fea_csr_rowptr_noalloc(const int32_t* counts, int64_t n, int64_t* rowptr, void* stream);
+
+/*
+ * fea_update_fields -- one step's change of the nodal field phi_old: a smooth seeded
+ * perturbation, in place,
+ *     phi[q][n] += A_q sin(kx_q x_n + ky_q y_n + kz_q z_n + psi_q)   (FP32),
+ * x_n the node's coordinates.  The paper steps its transport fields in time (Sec. 2) and
+ * reassembles every step; this perturbation stands in for the solver's update so that a
+ * run of steps sees changing fields.
+ *   phi     [n_eq][n_node] float DEVICE pointer, updated in place
+ *   params  [n_eq][5] float DEVICE pointer: A, kx, ky, kz, psi per equation (the caller
+ *           draws them; they are inputs, not generated here)
+ * Enqueued on the mesh's stream.
+ */
+FEA_API fea_status fea_update_fields(fea_mesh* mesh, void* phi, int32_t n_eq, const float* params);
+
+/*
+ * fea_graph_capture_steps -- records n_steps time steps, each "fea_assemble, then
+ * fea_update_fields with params + 5 n_eq s" (s = 0 .. n_steps-1), into one CUDA graph.
+ * Arguments are those of fea_assemble (FP32 precision only; accumulate must be 0), plus
+ *   params   [n_steps][n_eq][5] float DEVICE pointer, read at every launch
+ * Every pointer is baked into the graph: the arrays must stay allocated, and their
+ * contents at launch time are what the steps use.  Before recording, one eager assembly
+ * runs (it builds the schedules and scratch, which cannot be captured) and waits; its
+ * values/rhs are overwritten by the graph.  On success *out owns the graph.
+ */
+FEA_API fea_status fea_graph_capture_steps(fea_mesh* mesh, const fea_pattern* pattern, const void* velocity,
+                                           const void* diffusivity, const void* reaction, void* phi_old, double dt,
+                                           int32_t n_eq, const fea_assemble_opts* opts, void* values, void* rhs,
+                                           const float* params, int32_t n_steps, fea_graph** out);
+/* Launches the recorded steps on the mesh's current stream; returns without waiting. */
+FEA_API fea_status fea_graph_launch(fea_graph* graph);
+/* Frees the graph (the caller makes sure no launch of it is still running). */
+FEA_API fea_status fea_graph_destroy(fea_graph* graph);
 
 /* Thread-local message describing the last failure of a call on this thread. */
 FEA_API const char* fea_last_error(void);

@@ -70,6 +70,7 @@ def lib():
                                  _d, _d]
             L.or_row.restype = C.c_int64
             L.or_apply.argtypes = [_I, _d, _L, _i32, _L, _d, _d, _d, _d, _D, _I, _I, _d, _d]
+            L.or_update_fields.argtypes = [_d, _L, _I, _d, _d]
             _lib = L
     return _lib
 
@@ -220,3 +221,16 @@ def apply(elem_type, coords, conn, fields, q, x, terms=ALL_TERMS):
     if st:
         raise ValueError(f"oracle apply error {st}")
     return y
+
+
+def update_fields(coords, phi, params):
+    """One step's field update: returns phi + A sin(k . x + psi) per equation (FP64).
+    phi is (n_eq, N); params is (n_eq, 5) = A, kx, ky, kz, psi."""
+    out = np.array(phi, dtype=np.float64, copy=True, order="C")
+    p = _f(params).reshape(-1, 5)
+    if p.shape[0] != out.shape[0]:
+        raise ValueError("params must have one row per equation")
+    st = lib().or_update_fields(_f(coords).ravel(), out.shape[1], out.shape[0], p.ravel(), out.ravel())
+    if st:
+        raise ValueError(f"oracle update error {st}")
+    return out

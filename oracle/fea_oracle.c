@@ -553,3 +553,18 @@ int or_apply(int type, const double* coords, int64_t n_node, const int32_t* conn
   }
   return OR_OK;
 }
+
+/* Field update of one time step (the stepping reading of Sec. 2: fields change between
+ * assemblies): phi[q][n] += A_q sin(kx_q x_n + ky_q y_n + kz_q z_n + psi_q), params
+ * [n_eq][5] = A, kx, ky, kz, psi.  The definition written out, in double precision. */
+int or_update_fields(const double* coords, int64_t n_node, int n_eq, const double* params, double* phi) {
+  if (n_node < 0 || n_eq < 0) return OR_ERR_ARG;
+  for (int q = 0; q < n_eq; ++q) {
+    const double* p = params + 5 * q;
+    for (int64_t n = 0; n < n_node; ++n) {
+      const double* x = coords + 3 * n;
+      phi[q * n_node + n] += p[0] * sin(p[1] * x[0] + p[2] * x[1] + p[3] * x[2] + p[4]);
+    }
+  }
+  return OR_OK;
+}

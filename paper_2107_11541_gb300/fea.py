@@ -26,7 +26,8 @@ NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27}
 # Every symbol include/fea.h declares (checked by the tests).
 EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_destroy", "fea_mesh_set_stream", "fea_sync",
            "fea_pattern_build", "fea_pattern_get", "fea_pattern_destroy", "fea_assemble", "fea_assemble_host",
-           "fea_pack_plan", "fea_csr_rowptr_noalloc", "fea_last_error", "fea_kernel_launches", "fea_version"]
+           "fea_pack_plan", "fea_csr_rowptr_noalloc", "fea_update_fields", "fea_graph_capture_steps",
+           "fea_graph_launch", "fea_graph_destroy", "fea_last_error", "fea_kernel_launches", "fea_version"]
 
 
 class FeaError(RuntimeError):
@@ -66,6 +67,11 @@ def lib(path: str = LIB_PATH):
         L.fea_assemble_host.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(fea_assemble_opts), vp, vp]
         L.fea_pack_plan.argtypes = [vp, i32, i32, vp, vp]
         L.fea_csr_rowptr_noalloc.argtypes = [vp, i64, vp, vp]
+        L.fea_update_fields.argtypes = [vp, vp, i32, vp]
+        L.fea_graph_capture_steps.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(fea_assemble_opts), vp, vp,
+                                              vp, i32, C.POINTER(vp)]
+        L.fea_graph_launch.argtypes = [vp]
+        L.fea_graph_destroy.argtypes = [vp]
         L.fea_last_error.restype = C.c_char_p
         L.fea_version.restype = C.c_int32
         L.fea_kernel_launches.restype = C.c_int64
@@ -176,6 +182,30 @@ def fea_pack_plan(count_by_type, vector_size: int):
 def fea_csr_rowptr_noalloc(counts, n: int, rowptr, stream=None):
     """rowptr[n+1] (int64 CUDA tensor) from counts[n] (int32 CUDA tensor) without device allocation."""
     _check(lib().fea_csr_rowptr_noalloc(_ptr(counts), int(n), _ptr(rowptr), _stream_ptr(stream)))
+
+
+def fea_update_fields(mesh, phi, n_eq: int, params):
+    """phi [n_eq][N] float32 CUDA tensor, updated in place; params [n_eq][5] float32 CUDA tensor."""
+    _check(lib().fea_update_fields(mesh, _ptr(phi), int(n_eq), _ptr(params)))
+
+
+def fea_graph_capture_steps(mesh, pattern, velocity, diffusivity, reaction, phi_old, dt: float, n_eq: int, opts,
+                            values, rhs, params, n_steps: int) -> C.c_void_p:
+    """Records n_steps (assemble, update) steps in one CUDA graph; params [n_steps][n_eq][5] float32."""
+    out = C.c_void_p()
+    _check(lib().fea_graph_capture_steps(mesh, pattern, _ptr(velocity), _ptr(diffusivity), _ptr(reaction),
+                                         _ptr(phi_old), float(dt), int(n_eq),
+                                         C.byref(opts) if opts is not None else None, _ptr(values), _ptr(rhs),
+                                         _ptr(params), int(n_steps), C.byref(out)))
+    return out
+
+
+def fea_graph_launch(graph):
+    _check(lib().fea_graph_launch(graph))
+
+
+def fea_graph_destroy(graph):
+    _check(lib().fea_graph_destroy(graph))
 
 
 def fea_last_error() -> str:

@@ -178,6 +178,23 @@ def draw_fields(rng: np.random.Generator, coords: np.ndarray, n_eq: int, s_max: 
     return Fields(velocity_field(coords), k, s, p, dt)
 
 
+def step_params(n_steps: int, n_eq: int, seed: int = SEED_BASE + 1000) -> np.ndarray:
+    """Parameters of the per-step field perturbation, float32 [n_steps][n_eq][5]:
+    amplitude A ~ U[0.01, 0.05], wave vector k = 2 pi f d with f ~ U[0.5, 2] and d a
+    uniformly random unit direction, phase psi ~ U[0, 2 pi)."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((n_steps, n_eq, 5))
+    for s in range(n_steps):
+        for q in range(n_eq):
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            f = rng.uniform(0.5, 2.0)
+            out[s, q, 0] = rng.uniform(0.01, 0.05)
+            out[s, q, 1:4] = 2.0 * np.pi * f * d
+            out[s, q, 4] = rng.uniform(0.0, 2.0 * np.pi)
+    return out.astype(np.float32)
+
+
 @dataclasses.dataclass
 class Workload:
     name: str

@@ -512,6 +512,30 @@ def all_pins():
     return pins
 
 
+def test_field_update_closed_forms():
+    """The per-step perturbation at points where sin has a known value: zero amplitude
+    leaves phi unchanged; k = 0 adds A sin(psi) everywhere; on the plane k . x + psi = pi
+    the update vanishes, and a quarter period further it adds exactly A."""
+    rng = np.random.default_rng(5)
+    coords = rng.random((40, 3))
+    phi = rng.random((3, 40))
+    p = np.array([[0.0, 3.0, -1.0, 2.0, 0.7],      # A = 0
+                  [0.25, 0.0, 0.0, 0.0, np.pi / 6],  # k = 0: + A/2
+                  [0.5, 2.0, 0.0, 0.0, 0.0]])       # sin(2x)
+    out = O.update_fields(coords, phi, p)
+    assert np.array_equal(out[0], phi[0])
+    assert np.allclose(out[1], phi[1] + 0.125, rtol=0, atol=1e-15)
+    # nodes on x = pi/2 (2x = pi) and x = pi/4 (2x = pi/2)
+    c2 = np.array([[np.pi / 2, 0.3, 0.9], [np.pi / 4, 0.1, 0.2]])
+    o2 = O.update_fields(c2, np.zeros((3, 2)), p)
+    assert abs(o2[2, 0]) < 1e-15 and abs(o2[2, 1] - 0.5) < 1e-15
+    # linear in A; steps compose additively
+    half = p.copy()
+    half[:, 0] *= 0.5
+    twice = O.update_fields(coords, O.update_fields(coords, phi, half), half)
+    assert np.allclose(twice, out, rtol=0, atol=1e-14)
+
+
 MUTATIONS = {
     1: "diffusion term dropped",
     2: "convection sign flipped",
