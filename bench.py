@@ -351,6 +351,12 @@ def main():
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(args.workload, w, nnz),
            "clocks": clk, "gpu_launches": int(launches), "kernel_ms": kernel_ms, "roofline": roof,
            "roofline_other": other}
+    try:
+        sc, gr = fea.fea_tuned_strategy(p, q)
+        out["config"]["scatter"] = {1: "atomic", 2: "rowowned", 3: "gather"}.get(sc, str(sc))
+        out["config"]["eq_groups"] = gr
+    except fea.FeaError:
+        out["config"]["scatter"] = {0: "auto", 1: "atomic", 2: "rowowned", 3: "gather"}[args.scatter]
     if args.graph:
         out["graph"] = {"time_steps": args.steps, "launches": 1, "step": "assemble, then field update",
                         "update_ms": update_ms, "assemble_ms": kernel_ms}

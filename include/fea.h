@@ -85,7 +85,11 @@ enum {
 };
 
 typedef enum {
-  FEA_SCATTER_AUTO = 0,     /* pick per element type and size (autotuned) */
+  FEA_SCATTER_AUTO = 0,     /* autotuned: the first FP32 call for a pattern and equation count times
+                               the candidates (row-owned with 1-4 equation groups where available,
+                               gather, atomic; skipping those too large to try) and keeps the fastest.
+                               Not tuned while the stream is capturing or with accumulate = 1: then
+                               row-owned if available, else atomic */
   FEA_SCATTER_ATOMIC = 1,   /* element-parallel, atomic adds into zeroed outputs */
   FEA_SCATTER_ROWOWNED = 2, /* rows accumulated in shared memory and written once (deterministic) */
   FEA_SCATTER_GATHER = 3    /* FP32 only: element matrices to a device scratch buffer owned by the pattern,
@@ -103,7 +107,10 @@ typedef struct {
   void* event_begin;        /* optional cudaEvent_t recorded on the mesh stream just before the assembly
                                kernel(s), after any output zeroing; NULL = none */
   void* event_end;          /* optional cudaEvent_t recorded just after the assembly kernel(s) */
-  int32_t reserved[4];
+  int32_t eq_groups;        /* row-owned scatter: equations are assembled in this many groups (geometry
+                               recomputed per group, more rows per shared-memory window); 0 = 1, or the
+                               autotuned count under FEA_SCATTER_AUTO */
+  int32_t reserved[3];
 } fea_assemble_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -230,6 +237,13 @@ FEA_API fea_status fea_graph_capture_steps(fea_mesh* mesh, const fea_pattern* pa
 FEA_API fea_status fea_graph_launch(fea_graph* graph);
 /* Frees the graph (the caller makes sure no launch of it is still running). */
 FEA_API fea_status fea_graph_destroy(fea_graph* graph);
+
+/*
+ * fea_tuned_strategy -- the scatter (fea_scatter) and equation-group count that
+ * FEA_SCATTER_AUTO settled on for this pattern and n_eq.  FEA_ERR_STATE if no FP32
+ * FEA_SCATTER_AUTO call has tuned that equation count yet.  Host only; does not wait.
+ */
+FEA_API fea_status fea_tuned_strategy(const fea_pattern* pattern, int32_t n_eq, int32_t* scatter, int32_t* eq_groups);
 
 /* Thread-local message describing the last failure of a call on this thread. */
 FEA_API const char* fea_last_error(void);

@@ -396,6 +396,160 @@ static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, 
 }
 
 
+
+// ------------------------------------------------------------------ strategies and the autotuner
+
+namespace {
+
+struct Strategy {
+  int scatter;  // fea_scatter, never AUTO here except before resolution
+  int groups;   // equation groups of the row-owned scatter
+};
+
+bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// Runs one assembly with a resolved strategy (FP64: always the plain per-equation path).
+fea_status run_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const void* kd, const void* sr, const void* phi,
+                        double dt, int32_t n_eq, const fea_assemble_opts& o, void* values, void* rhs,
+                        Strategy st) {
+  cudaStream_t s = m->stream;
+  size_t es = o.precision == FEA_F64_PLAIN ? sizeof(double) : sizeof(float);
+  const bool f32 = o.precision == FEA_F32_FUSED;
+  bool rowowned = false;
+  if (f32 && (st.scatter == FEA_SCATTER_ROWOWNED || st.scatter == FEA_SCATTER_AUTO)) {
+    FEA_TRY(plan_prepare(p->plan, plan_group_size(n_eq, st.groups), &rowowned));
+    if (st.scatter == FEA_SCATTER_ROWOWNED && !rowowned)
+      return fail(FEA_ERR_ARG, "row-owned scatter is not available for this mesh type, precision or equation count");
+  }
+  const bool gather = f32 && st.scatter == FEA_SCATTER_GATHER;
+  if (gather && m->n_elem > 0) {
+    const size_t need = gather_scratch_bytes(m->n_elem, m->nen, n_eq);
+    if (p->em_bytes < need) {
+      if (stream_capturing(s)) return fail(FEA_ERR_STATE, "gather scratch must be allocated before stream capture");
+      FEA_CUDA_TRY(cudaStreamSynchronize(s));  // the old scratch may still be in use on the stream
+      cudaFree(p->em);
+      p->em = nullptr;
+      p->em_bytes = 0;
+      if (cudaMalloc(&p->em, need) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FEA_ERR_OOM, "gather scatter: %zu bytes of element-matrix scratch", need);
+      }
+      p->em_bytes = need;
+    }
+  }
+  if (!o.accumulate && !rowowned && !(gather && m->n_elem > 0)) {
+    FEA_CUDA_TRY(cudaMemsetAsync(values, 0, es * (size_t)n_eq * (size_t)p->nnz, s));
+    FEA_CUDA_TRY(cudaMemsetAsync(rhs, 0, es * (size_t)n_eq * (size_t)m->n_node, s));
+  }
+  if (o.event_begin) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_begin, s));
+  if (m->n_elem > 0) {
+    if (!f32) {
+      AsmArgs<double> a = make_args<double>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
+      for (int q = 0; q < n_eq; ++q) {  // one launch per equation, geometry recomputed each time
+        a.eq0 = q;
+        a.eq_count = 1;
+        FEA_TRY(launch_generic_f64(a, m->type, s));
+      }
+    } else {
+      AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
+      if (rowowned) {
+        FEA_TRY(plan_assemble(p->plan, a, o.accumulate, st.groups, s));
+      } else if (gather) {
+        a.em = (float*)p->em;
+        FEA_TRY(launch_generic_f32(a, m->type, s));
+        FEA_TRY(launch_gather_f32(a, m->type, p->maxcol, o.accumulate != 0, s));
+      } else {
+        FEA_TRY(launch_generic_f32(a, m->type, s));
+      }
+    }
+  }
+  if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, s));
+  return FEA_OK;
+}
+
+// Resolves FEA_SCATTER_AUTO for an FP32 call.  The first call for a pattern and equation
+// count times every candidate on the caller's own inputs (each result overwrites values and
+// rhs, so the outputs end up assembled whichever ran last) and caches the fastest.
+fea_status choose_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const void* kd, const void* sr,
+                           const void* phi, double dt, int32_t n_eq, const fea_assemble_opts& o, void* values,
+                           void* rhs, Strategy* out) {
+  auto it = p->tuned.find(n_eq);
+  if (it != p->tuned.end()) {
+    *out = Strategy{it->second.first, it->second.second};
+    return FEA_OK;
+  }
+  bool ro1 = false;
+  FEA_TRY(plan_prepare(p->plan, n_eq, &ro1));
+  const Strategy fallback{ro1 ? FEA_SCATTER_ROWOWNED : FEA_SCATTER_ATOMIC, 1};
+  if (o.accumulate || m->n_elem == 0 || stream_capturing(m->stream)) {  // cannot run trials
+    *out = fallback;
+    return FEA_OK;
+  }
+  std::vector<Strategy> cand;
+  int last_size = -1;
+  for (int g = 1; g <= 4 && g <= n_eq; ++g) {
+    const int size = plan_group_size(n_eq, g);
+    if (size == last_size) continue;
+    last_size = size;
+    bool ok = false;
+    FEA_TRY(plan_prepare(p->plan, size, &ok));
+    if (ok) cand.push_back(Strategy{FEA_SCATTER_ROWOWNED, g});
+  }
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  if (gather_scratch_bytes(m->n_elem, m->nen, n_eq) <= free_b / 2) cand.push_back(Strategy{FEA_SCATTER_GATHER, 1});
+  // atomics into DRAM run at a few G/s: try them only where a trial stays short
+  if ((double)m->n_elem * m->nen * m->nen * n_eq < 2e9 || cand.empty())
+    cand.push_back(Strategy{FEA_SCATTER_ATOMIC, 1});
+
+  fea_assemble_opts oq = o;
+  oq.event_begin = oq.event_end = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FEA_CUDA_TRY(cudaEventCreate(&e0));
+  FEA_CUDA_TRY(cudaEventCreate(&e1));
+  Strategy best = fallback;
+  float best_ms = 0.f;
+  fea_status status = FEA_OK;
+  for (const Strategy& c : cand) {
+    float ms = 0.f;
+    fea_status s1 = run_strategy(m, p, vel, kd, sr, phi, dt, n_eq, oq, values, rhs, c);  // warm-up
+    if (s1 == FEA_OK) s1 = fea_sync(m);
+    if (s1 == FEA_OK && cudaEventRecord(e0, m->stream) != cudaSuccess) s1 = FEA_ERR_CUDA;
+    if (s1 == FEA_OK) s1 = run_strategy(m, p, vel, kd, sr, phi, dt, n_eq, oq, values, rhs, c);
+    if (s1 == FEA_OK && cudaEventRecord(e1, m->stream) != cudaSuccess) s1 = FEA_ERR_CUDA;
+    if (s1 == FEA_OK) s1 = fea_sync(m);
+    if (s1 == FEA_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) s1 = FEA_ERR_CUDA;
+    if (s1 == FEA_ERR_OOM) continue;  // a candidate that does not fit is skipped
+    if (s1 != FEA_OK) {
+      status = s1;
+      break;
+    }
+    if (best_ms == 0.f || ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status != FEA_OK) return status;
+  // keep the winner's resources only
+  if (best.scatter == FEA_SCATTER_ROWOWNED) plan_trim(p->plan, plan_group_size(n_eq, best.groups));
+  else plan_trim(p->plan, -1);
+  if (best.scatter != FEA_SCATTER_GATHER) {
+    cudaFree(p->em);
+    p->em = nullptr;
+    p->em_bytes = 0;
+  }
+  p->tuned[n_eq] = std::make_pair(best.scatter, best.groups);
+  *out = best;
+  return FEA_OK;
+}
+
+}  // namespace
+
 // ------------------------------------------------------------------ C ABI
 
 extern "C" {
@@ -607,56 +761,18 @@ fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, cons
   if (opts) o = *opts;
   else fea_default_opts(&o);
   FEA_TRY(check_assemble_args(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs));
-  cudaStream_t s = m->stream;
-  size_t es = o.precision == FEA_F64_PLAIN ? sizeof(double) : sizeof(float);
-  bool rowowned = false;
-  if (o.precision == FEA_F32_FUSED && (o.scatter == FEA_SCATTER_AUTO || o.scatter == FEA_SCATTER_ROWOWNED))
-    FEA_TRY(plan_prepare(p->plan, n_eq, &rowowned));
-  if (o.scatter == FEA_SCATTER_ROWOWNED && !rowowned)
-    return fail(FEA_ERR_ARG, "row-owned scatter is not available for this mesh type, precision or equation count");
-  const bool gather = o.scatter == FEA_SCATTER_GATHER;
-  if (gather && m->n_elem > 0) {
-    fea_pattern* pw = const_cast<fea_pattern*>(p);  // the scratch belongs to the pattern
-    const size_t need = gather_scratch_bytes(m->n_elem, m->nen, n_eq);
-    if (pw->em_bytes < need) {
-      FEA_CUDA_TRY(cudaStreamSynchronize(s));  // the old scratch may still be in use on the stream
-      cudaFree(pw->em);
-      pw->em = nullptr;
-      pw->em_bytes = 0;
-      if (cudaMalloc(&pw->em, need) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(FEA_ERR_OOM, "gather scatter: %zu bytes of element-matrix scratch", need);
-      }
-      pw->em_bytes = need;
-    }
-  }
-  if (!o.accumulate && !rowowned && !(gather && m->n_elem > 0)) {
-    FEA_CUDA_TRY(cudaMemsetAsync(values, 0, es * (size_t)n_eq * (size_t)p->nnz, s));
-    FEA_CUDA_TRY(cudaMemsetAsync(rhs, 0, es * (size_t)n_eq * (size_t)m->n_node, s));
-  }
-  if (o.event_begin) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_begin, s));
-  if (m->n_elem > 0) {
-    if (o.precision == FEA_F64_PLAIN) {
-      AsmArgs<double> a = make_args<double>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
-      for (int q = 0; q < n_eq; ++q) {  // one launch per equation, geometry recomputed each time
-        a.eq0 = q;
-        a.eq_count = 1;
-        FEA_TRY(launch_generic_f64(a, m->type, s));
-      }
-    } else {
-      AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
-      if (rowowned) {
-        FEA_TRY(plan_assemble(p->plan, a, o.accumulate, s));
-      } else if (gather) {
-        a.em = (float*)p->em;
-        FEA_TRY(launch_generic_f32(a, m->type, s));
-        FEA_TRY(launch_gather_f32(a, m->type, p->maxcol, o.accumulate != 0, s));
-      } else {
-        FEA_TRY(launch_generic_f32(a, m->type, s));
-      }
-    }
-  }
-  if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, s));
+  fea_pattern* pw = const_cast<fea_pattern*>(p);  // schedules, scratch and the tuning cache belong to the pattern
+  Strategy st{o.scatter, std::max(1, o.eq_groups)};
+  if (o.precision == FEA_F32_FUSED && o.scatter == FEA_SCATTER_AUTO) FEA_TRY(choose_strategy(m, pw, vel, kd, sr, phi, dt, n_eq, o, values, rhs, &st));
+  return run_strategy(m, pw, vel, kd, sr, phi, dt, n_eq, o, values, rhs, st);
+}
+
+fea_status fea_tuned_strategy(const fea_pattern* p, int32_t n_eq, int32_t* scatter, int32_t* eq_groups) {
+  if (!p || !scatter || !eq_groups) return fail(FEA_ERR_ARG, "fea_tuned_strategy: null argument");
+  auto it = p->tuned.find(n_eq);
+  if (it == p->tuned.end()) return fail(FEA_ERR_STATE, "no tuned strategy for %d equations yet", n_eq);
+  *scatter = it->second.first;
+  *eq_groups = it->second.second;
   return FEA_OK;
 }
 

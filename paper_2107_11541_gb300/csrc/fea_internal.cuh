@@ -8,7 +8,10 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <map>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "fea.h"
 
@@ -81,6 +84,8 @@ struct fea_pattern {
   // element-matrix scratch of the gather scatter, grown on demand
   void* em;
   size_t em_bytes;
+  // autotuned strategy per equation count: {scatter, equation groups}
+  std::map<int, std::pair<int, int>> tuned;
   // device workspace for fea_assemble_host
   void* ws;
   size_t ws_bytes;

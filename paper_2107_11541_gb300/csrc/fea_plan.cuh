@@ -12,6 +12,11 @@ void plan_destroy(fea_rowowned_plan* plan);
 // Builds, on first use, the schedule for n_eq equations.  *ok is false when the
 // row-owned kernel cannot serve this call (the atomic path is used instead).
 fea_status plan_prepare(fea_rowowned_plan* plan, int n_eq, bool* ok);
-fea_status plan_assemble(fea_rowowned_plan* plan, const AsmArgs<float>& a, int accumulate, cudaStream_t s);
+// Equations a.eq0 .. a.eq0 + a.eq_count - 1 in `groups` groups of plan_group_size(eq_count, groups)
+// (the last one smaller); plan_prepare must have succeeded for that group size.
+fea_status plan_assemble(fea_rowowned_plan* plan, const AsmArgs<float>& a, int accumulate, int groups, cudaStream_t s);
+int plan_group_size(int n_eq, int groups);
+// Frees the schedules of every group size but keep_n_eq.
+void plan_trim(fea_rowowned_plan* plan, int keep_n_eq);
 
 }  // namespace fea

@@ -32,7 +32,7 @@ namespace fea {
 namespace ro {
 
 constexpr int NEN = 8, NG = 8;
-constexpr int BEMAX = 24;               // elements per batch at most: geometry uses <= 6 warps, >= 2 flush
+constexpr int BEMAX = 32;               // elements per batch at most: geometry uses <= 6 warps, >= 2 flush
 constexpr int THREADS = 256;            // 8 warps
 constexpr int ROUNDS = 4;               // scatter rounds: local rows a and a + 4 in round a & 3
 constexpr int round_of(int a) { return a & 3; }
@@ -473,16 +473,30 @@ __global__ void k_fields_nodemajor(const float* __restrict__ kd, const float* __
 }
 }  // namespace ro
 
-fea_status plan_assemble(fea_rowowned_plan* P, const AsmArgs<float>& a, int accumulate, cudaStream_t s) {
-  ro::Variant* v = P->variants.at(a.n_eq);
-  if (v->unused_nodes && !accumulate)
-    FEA_CUDA_TRY(cudaMemsetAsync(a.rhs, 0, sizeof(float) * (size_t)a.n_eq * (size_t)a.n_node, s));
-  const int rec = 3 * a.n_eq + 3;
+int plan_group_size(int n_eq, int groups) { return (n_eq + groups - 1) / groups; }
+
+void plan_trim(fea_rowowned_plan* P, int keep_n_eq) {
+  if (!P) return;
+  std::lock_guard<std::mutex> lk(P->mu);
+  for (auto it = P->variants.begin(); it != P->variants.end();) {
+    if (it->first != keep_n_eq) {
+      ro::free_variant(it->second);
+      it = P->variants.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+// One group of equations [a.eq0, a.eq0 + a.eq_count) with the schedule of variant v.
+static fea_status assemble_group(ro::Variant* v, const AsmArgs<float>& a, int accumulate, cudaStream_t s) {
+  const int rec = 3 * a.eq_count + 3;
+  const int64_t fo = (int64_t)a.eq0 * a.n_node;
   {
     const size_t tsm = sizeof(float) * rec * 33;
     FEA_CUDA_TRY(cudaFuncSetAttribute(ro::k_fields_nodemajor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    ro::k_fields_nodemajor<<<(unsigned)((a.n_node + 31) / 32), 256, tsm, s>>>(a.kd, a.sr, a.phi, a.vel, a.n_node,
-                                                                              a.n_eq, v->fnode);
+    ro::k_fields_nodemajor<<<(unsigned)((a.n_node + 31) / 32), 256, tsm, s>>>(a.kd + fo, a.sr + fo, a.phi + fo, a.vel,
+                                                                              a.n_node, a.eq_count, v->fnode);
     FEA_CUDA_TRY(cudaGetLastError());
     count_launches(1);
   }
@@ -512,6 +526,23 @@ fea_status plan_assemble(fea_rowowned_plan* P, const AsmArgs<float>& a, int accu
   kern<<<grid, ro::THREADS, v->smem, s>>>(r);
   FEA_CUDA_TRY(cudaGetLastError());
   count_launches(1);
+  return FEA_OK;
+}
+
+fea_status plan_assemble(fea_rowowned_plan* P, const AsmArgs<float>& a, int accumulate, int groups, cudaStream_t s) {
+  const int gsize = plan_group_size(a.eq_count, groups);
+  ro::Variant* v = P->variants.at(gsize);
+  if (v->unused_nodes && !accumulate)
+    FEA_CUDA_TRY(cudaMemsetAsync(a.rhs + (int64_t)a.eq0 * a.n_node, 0,
+                                 sizeof(float) * (size_t)a.eq_count * (size_t)a.n_node, s));
+  // equations in groups of gsize: the geometry is recomputed per group, the row window of a
+  // group holds gsize equations per row, so more rows fit (larger tiles, fuller batches)
+  for (int g0 = 0; g0 < a.eq_count; g0 += gsize) {
+    AsmArgs<float> ag = a;
+    ag.eq0 = a.eq0 + g0;
+    ag.eq_count = std::min(gsize, a.eq_count - g0);
+    FEA_TRY(assemble_group(v, ag, accumulate, s));
+  }
   return FEA_OK;
 }
 

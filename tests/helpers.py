@@ -41,7 +41,7 @@ class GpuRun:
         return dev, dt
 
     def assemble(self, fields: G.Fields, precision: int, terms=fea.FEA_TERM_ALL, scatter=fea.FEA_SCATTER_AUTO,
-                 accumulate=0, out=None):
+                 accumulate=0, out=None, eq_groups=0):
         torch = self.torch
         (vel, kd, sr, phi), dt = self.upload(fields, precision)
         q = fields.n_eq
@@ -50,7 +50,8 @@ class GpuRun:
             rhs = torch.full((q, self.mesh.n_node), float("nan"), dtype=dt, device="cuda")
         else:
             values, rhs = out
-        opts = fea.fea_default_opts(precision=precision, terms=terms, scatter=scatter, accumulate=accumulate)
+        opts = fea.fea_default_opts(precision=precision, terms=terms, scatter=scatter, accumulate=accumulate,
+                                    eq_groups=eq_groups)
         fea.fea_assemble(self.handle, self.pattern, vel, kd, sr, phi, fields.dt, q, opts, values, rhs)
         fea.fea_sync(self.handle)
         return values, rhs

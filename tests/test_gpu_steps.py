@@ -37,7 +37,7 @@ def test_update_fields_matches_oracle():
         run.close()
 
 
-@pytest.mark.parametrize("cfg,n,q,scatter", [(2, 6, 4, fea.FEA_SCATTER_AUTO), (1, 5, 2, fea.FEA_SCATTER_GATHER),
+@pytest.mark.parametrize("cfg,n,q,scatter", [(2, 6, 4, fea.FEA_SCATTER_ROWOWNED), (1, 5, 2, fea.FEA_SCATTER_GATHER),
                                              (3, 2, 2, fea.FEA_SCATTER_GATHER)],
                          ids=["hex8_rowowned", "tet4_gather", "hex27_gather"])
 def test_graph_equals_eager_steps_and_oracle(cfg, n, q, scatter):
