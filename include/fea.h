@@ -110,7 +110,9 @@ typedef struct {
   int32_t eq_groups;        /* row-owned scatter: equations are assembled in this many groups (geometry
                                recomputed per group, more rows per shared-memory window); 0 = 1, or the
                                autotuned count under FEA_SCATTER_AUTO */
-  int32_t reserved[3];
+  int32_t cancel_check;     /* FP32 path: 1 = rows whose sums cancel are redone in FP64 (see
+                               fea_cancel_rows); not allowed with accumulate.  Default 0 */
+  int32_t reserved[2];
 } fea_assemble_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -244,6 +246,18 @@ FEA_API fea_status fea_graph_destroy(fea_graph* graph);
  * FEA_SCATTER_AUTO call has tuned that equation count yet.  Host only; does not wait.
  */
 FEA_API fea_status fea_tuned_strategy(const fea_pattern* pattern, int32_t n_eq, int32_t* scatter, int32_t* eq_groups);
+
+/*
+ * fea_cancel_rows -- the cancellation check (opts.cancel_check = 1, FP32 path).  Row i of an
+ * equation is flagged when an entry with |A_ij| > 1e-3 max_j |A_ij| has
+ * sum_e |A^e_ij| > 1e3 |A_ij|, or when sum_e |b^e_i| > 1e3 |b_i| (the sums over the elements
+ * containing the row's node).  The first checked assembly for a pattern and n_eq computes the
+ * flags in one FP32 pass over all rows (it waits for the GPU; it cannot run under stream
+ * capture) and keeps them while the pattern lives; every checked assembly then recomputes the
+ * flagged rows, element rows formed and summed in FP64 from the same inputs, after the main
+ * assembly.  *count = number of flagged rows; FEA_ERR_STATE before the first checked call.
+ */
+FEA_API fea_status fea_cancel_rows(const fea_pattern* pattern, int32_t n_eq, int64_t* count);
 
 /* Thread-local message describing the last failure of a call on this thread. */
 FEA_API const char* fea_last_error(void);

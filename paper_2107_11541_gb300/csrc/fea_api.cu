@@ -358,6 +358,8 @@ static fea_status check_assemble_args(fea_mesh* m, const fea_pattern* p, const v
   if (o->scatter < FEA_SCATTER_AUTO || o->scatter > FEA_SCATTER_GATHER) return fail(FEA_ERR_ARG, "unknown scatter");
   if (o->scatter == FEA_SCATTER_GATHER && o->precision != FEA_F32_FUSED)
     return fail(FEA_ERR_ARG, "the gather scatter is an FP32 path");
+  if (o->cancel_check != 0 && o->cancel_check != 1) return fail(FEA_ERR_ARG, "cancel_check must be 0 or 1");
+  if (o->cancel_check && o->accumulate) return fail(FEA_ERR_ARG, "cancel_check cannot be combined with accumulate");
   return FEA_OK;
 }
 
@@ -670,6 +672,7 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->inc_elem);
   cudaFree(p->ws);
   cudaFree(p->em);
+  for (auto& kv : p->cancel) cudaFree(kv.second.first);
   plan_destroy(p->plan);
   delete p;
   return FEA_OK;
@@ -763,8 +766,35 @@ fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, cons
   FEA_TRY(check_assemble_args(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs));
   fea_pattern* pw = const_cast<fea_pattern*>(p);  // schedules, scratch and the tuning cache belong to the pattern
   Strategy st{o.scatter, std::max(1, o.eq_groups)};
-  if (o.precision == FEA_F32_FUSED && o.scatter == FEA_SCATTER_AUTO) FEA_TRY(choose_strategy(m, pw, vel, kd, sr, phi, dt, n_eq, o, values, rhs, &st));
-  return run_strategy(m, pw, vel, kd, sr, phi, dt, n_eq, o, values, rhs, st);
+  if (o.precision == FEA_F32_FUSED && o.scatter == FEA_SCATTER_AUTO)
+    FEA_TRY(choose_strategy(m, pw, vel, kd, sr, phi, dt, n_eq, o, values, rhs, &st));
+  const bool check = o.cancel_check && o.precision == FEA_F32_FUSED && m->n_elem > 0;
+  if (!check) return run_strategy(m, pw, vel, kd, sr, phi, dt, n_eq, o, values, rhs, st);
+  // the main assembly, then the FP64 recomputation of the flagged rows (inside the events)
+  fea_assemble_opts om = o;
+  om.event_end = nullptr;
+  FEA_TRY(run_strategy(m, pw, vel, kd, sr, phi, dt, n_eq, om, values, rhs, st));
+  AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
+  auto it = pw->cancel.find(n_eq);
+  if (it == pw->cancel.end()) {
+    if (stream_capturing(m->stream))
+      return fail(FEA_ERR_STATE, "the cancellation flags must be computed by a checked call before stream capture");
+    int32_t* rows = nullptr;
+    int64_t count = 0;
+    FEA_TRY(cancel_flag_rows(a, m->type, p->maxcol, &rows, &count, m->stream));
+    it = pw->cancel.emplace(n_eq, std::make_pair(rows, count)).first;
+  }
+  FEA_TRY(cancel_fix_rows(a, m->type, p->maxcol, it->second.first, it->second.second, m->stream));
+  if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, m->stream));
+  return FEA_OK;
+}
+
+fea_status fea_cancel_rows(const fea_pattern* p, int32_t n_eq, int64_t* count) {
+  if (!p || !count) return fail(FEA_ERR_ARG, "fea_cancel_rows: null argument");
+  auto it = p->cancel.find(n_eq);
+  if (it == p->cancel.end()) return fail(FEA_ERR_STATE, "no checked assembly for %d equations yet", n_eq);
+  *count = it->second.second;
+  return FEA_OK;
 }
 
 fea_status fea_tuned_strategy(const fea_pattern* p, int32_t n_eq, int32_t* scatter, int32_t* eq_groups) {

@@ -86,6 +86,8 @@ struct fea_pattern {
   size_t em_bytes;
   // autotuned strategy per equation count: {scatter, equation groups}
   std::map<int, std::pair<int, int>> tuned;
+  // cancellation check per equation count: {device list of flagged rows, count}
+  std::map<int, std::pair<int32_t*, int64_t>> cancel;
   // device workspace for fea_assemble_host
   void* ws;
   size_t ws_bytes;
@@ -243,5 +245,11 @@ fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStre
 fea_status launch_gather_f32(const AsmArgs<float>& a, fea_elem_t type, int maxcol, bool accumulate, cudaStream_t s);
 // Bytes of element-matrix scratch the gather scatter needs.
 size_t gather_scratch_bytes(int64_t n_elem, int nen, int n_eq);
+// Cancellation check: one FP32 pass flags rows (device list, owned by the caller afterwards,
+// and its length; waits for the GPU), and the FP64 recomputation of the listed rows.
+fea_status cancel_flag_rows(const AsmArgs<float>& a, fea_elem_t type, int maxcol, int32_t** rows, int64_t* count,
+                            cudaStream_t s);
+fea_status cancel_fix_rows(const AsmArgs<float>& a, fea_elem_t type, int maxcol, const int32_t* rows, int64_t count,
+                           cudaStream_t s);
 
 }  // namespace fea

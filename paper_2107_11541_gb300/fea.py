@@ -27,8 +27,8 @@ NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27}
 EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_destroy", "fea_mesh_set_stream", "fea_sync",
            "fea_pattern_build", "fea_pattern_get", "fea_pattern_destroy", "fea_assemble", "fea_assemble_host",
            "fea_pack_plan", "fea_csr_rowptr_noalloc", "fea_update_fields", "fea_graph_capture_steps",
-           "fea_graph_launch", "fea_graph_destroy", "fea_tuned_strategy", "fea_last_error", "fea_kernel_launches",
-           "fea_version"]
+           "fea_graph_launch", "fea_graph_destroy", "fea_tuned_strategy", "fea_cancel_rows", "fea_last_error",
+           "fea_kernel_launches", "fea_version"]
 
 
 class FeaError(RuntimeError):
@@ -41,7 +41,7 @@ class FeaError(RuntimeError):
 class fea_assemble_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("terms", C.c_int32), ("scatter", C.c_int32), ("accumulate", C.c_int32),
                 ("kappa_threshold", C.c_double), ("event_begin", C.c_void_p), ("event_end", C.c_void_p),
-                ("eq_groups", C.c_int32), ("reserved", C.c_int32 * 3)]
+                ("eq_groups", C.c_int32), ("cancel_check", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 _lib = None
@@ -73,6 +73,7 @@ def lib(path: str = LIB_PATH):
                                               vp, i32, C.POINTER(vp)]
         L.fea_graph_launch.argtypes = [vp]
         L.fea_tuned_strategy.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
+        L.fea_cancel_rows.argtypes = [vp, i32, C.POINTER(i64)]
         L.fea_graph_destroy.argtypes = [vp]
         L.fea_last_error.restype = C.c_char_p
         L.fea_version.restype = C.c_int32
@@ -215,6 +216,13 @@ def fea_tuned_strategy(pattern, n_eq: int):
     s, g = C.c_int32(), C.c_int32()
     _check(lib().fea_tuned_strategy(pattern, int(n_eq), C.byref(s), C.byref(g)))
     return s.value, g.value
+
+
+def fea_cancel_rows(pattern, n_eq: int) -> int:
+    """Number of rows the cancellation check flagged for this pattern and equation count."""
+    n = C.c_int64()
+    _check(lib().fea_cancel_rows(pattern, int(n_eq), C.byref(n)))
+    return n.value
 
 
 def fea_last_error() -> str:
