@@ -97,9 +97,37 @@ __device__ TC warp_geometry(const AsmArgs<TI>& p, int64_t e, TC* S, const TC* Nt
         for (int j = 0; j < 3; ++j) J[i][j] += S[L::XE + a * 3 + i] * dN[j];
     }
     TC det = det3(J);
-    if (!(det > TC(0))) atomicOr(p.status, ST_INVERTED);
     TC G[3][3];
     inv_transpose3(J, det, G);
+    if constexpr (sizeof(TC) == 4) {
+      // condition estimate |J|_F |J^-1|_F / 3; above the threshold (or det <= 0 in FP32) det and
+      // J^-1 are redone in FP64 from the FP64 coordinates
+      TC nj = 0, ni = 0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+          nj += J[i][j] * J[i][j];
+          ni += G[i][j] * G[i][j];
+        }
+      if (!(det > TC(0)) || !(nj * ni <= TC(9) * (TC)(p.kappa_threshold * p.kappa_threshold))) {
+        double Jd[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Gd[3][3];
+        for (int a = 0; a < NEN; ++a) {
+          double Nd, dNd[3];
+          shape<TYPE>(a, xid, Nd, dNd);
+          for (int i = 0; i < 3; ++i) {
+            const double xa = p.coords[(int64_t)node[a] * 3 + i] - p.coords[(int64_t)n0 * 3 + i];
+            for (int j = 0; j < 3; ++j) Jd[i][j] += xa * dNd[j];
+          }
+        }
+        const double dd = det3(Jd);
+        if (!(dd > 0.0)) atomicOr(p.status, ST_INVERTED);
+        inv_transpose3(Jd, dd, Gd);
+        det = (TC)dd;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) G[i][j] = (TC)Gd[i][j];
+      }
+    } else {
+      if (!(det > TC(0))) atomicOr(p.status, ST_INVERTED);
+    }
     TC ug[3] = {0, 0, 0};
     for (int a = 0; a < NEN; ++a) {
       TC Na = Nt[g * NEN + a];

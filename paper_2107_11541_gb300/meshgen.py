@@ -133,9 +133,13 @@ def interior_mask(mesh: Mesh) -> np.ndarray:
     return np.all((c > 0.0) & (c < 1.0), axis=1)
 
 
-def perturb_interior(mesh: Mesh, rng: np.random.Generator, frac: float) -> None:
-    """Move interior nodes by U[-frac*h, frac*h] per coordinate (boundary stays planar)."""
+def perturb_interior(mesh: Mesh, rng: np.random.Generator, frac: float, move_z: bool = True) -> None:
+    """Move interior nodes by U[-frac*h, frac*h] per coordinate (boundary stays planar);
+    with move_z False the z displacement is drawn but not applied (meshes whose z spacing
+    is not uniform, where h-sized moves in z would invert the thin cells)."""
     d = rng.uniform(-frac * mesh.h, frac * mesh.h, size=mesh.coords.shape)
+    if not move_z:
+        d[:, 2] = 0.0
     mask = interior_mask(mesh)
     if frac > 0.0:
         mesh.coords[mask] += d[mask]
@@ -244,7 +248,7 @@ def make_workload(index: int, n: int | None = None, n_eq: int | None = None, see
         z_faces = faces
     mesh = structured_mesh(et, nc, z_faces)
     if cfg["frac"] > 0.0:
-        perturb_interior(mesh, rng, cfg["frac"])
+        perturb_interior(mesh, rng, cfg["frac"], move_z=not stretched_slab)
     else:
         rng.uniform(size=mesh.coords.shape)  # keep the draw order fixed
     if cfg["permute"]:

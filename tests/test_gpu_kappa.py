@@ -1,0 +1,50 @@
+"""FP64 Jacobians for badly conditioned elements (FP32 path), through the C ABI.
+
+A mesh with one slab of elements 1e4 times thinner than the rest, rotated off the axes so
+that the thin direction mixes all three coordinates: in FP32 the cofactor inverse of such a
+Jacobian loses about kappa * 6e-8 of relative accuracy.  Gauss points whose condition estimate
+exceeds opts.kappa_threshold (default 1e3) get det J and J^-1 in FP64; with the fallback on,
+every scatter stays within the FP32 tolerance."""
+import numpy as np
+import pytest
+
+from helpers import TOL_F32, GpuRun, compare_full
+from paper_2107_11541_gb300 import fea
+from paper_2107_11541_gb300 import meshgen as G
+
+pytestmark = pytest.mark.gpu
+
+
+def rotated_slab(cfg, n, q):
+    w = G.make_workload(cfg, n=n, n_eq=q, stretched_slab=True)
+    a, b, c = 0.3, 0.5, 0.7
+    rx = np.array([[1, 0, 0], [0, np.cos(a), -np.sin(a)], [0, np.sin(a), np.cos(a)]])
+    ry = np.array([[np.cos(b), 0, np.sin(b)], [0, 1, 0], [-np.sin(b), 0, np.cos(b)]])
+    rz = np.array([[np.cos(c), -np.sin(c), 0], [np.sin(c), np.cos(c), 0], [0, 0, 1]])
+    w.mesh.coords = w.mesh.coords @ (rz @ ry @ rx).T
+    return w
+
+
+@pytest.mark.parametrize("cfg,n,q,scatter", [(2, 6, 2, fea.FEA_SCATTER_ROWOWNED), (2, 6, 2, fea.FEA_SCATTER_GATHER),
+                                             (3, 3, 2, fea.FEA_SCATTER_ATOMIC), (3, 3, 2, fea.FEA_SCATTER_GATHER)],
+                         ids=["hex8_rowowned", "hex8_gather", "hex27_atomic", "hex27_gather"])
+def test_kappa_fallback_keeps_fp32_parity(cfg, n, q, scatter):
+    import torch
+    w = rotated_slab(cfg, n, q)
+    run = GpuRun(w.mesh)
+    try:
+        errs = {}
+        for kappa in (1e3, 1e30):
+            (vel, kd, sr, phi), _ = run.upload(w.fields, fea.FEA_F32_FUSED)
+            vals = torch.empty((q, run.nnz), device="cuda")
+            rhs = torch.empty((q, w.mesh.n_node), device="cuda")
+            opts = fea.fea_default_opts(scatter=scatter, kappa_threshold=kappa)
+            fea.fea_assemble(run.handle, run.pattern, vel, kd, sr, phi, w.fields.dt, q, opts, vals, rhs)
+            fea.fea_sync(run.handle)
+            errs[kappa] = compare_full(run, w.fields, fea.FEA_F32_FUSED, values=vals, rhs=rhs)
+        ea, eb = errs[1e3]
+        assert ea <= TOL_F32 and eb <= TOL_F32, errs
+        # without the fallback the thin elements' FP32 inverse is visibly worse
+        assert errs[1e30][0] > ea, errs
+    finally:
+        run.close()
