@@ -241,6 +241,8 @@ struct AsmArgs {
 // Launchers (defined in the kernel translation units).
 fea_status launch_generic_f64(const AsmArgs<double>& a, fea_elem_t type, cudaStream_t s);
 fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s);
+// FP32 Tet4: one thread per (element, equation) (atomics, or the gather scratch if a.em).
+fea_status launch_tet4_f32(const AsmArgs<float>& a, cudaStream_t s);
 // Row gather of the element matrices in a.em into a.values / a.rhs (overwrite or add).
 fea_status launch_gather_f32(const AsmArgs<float>& a, fea_elem_t type, int maxcol, bool accumulate, cudaStream_t s);
 // Bytes of element-matrix scratch the gather scatter needs.
