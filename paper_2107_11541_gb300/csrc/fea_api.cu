@@ -310,6 +310,18 @@ k_rows(const int32_t* __restrict__ conn, int nen, const int64_t* __restrict__ in
   }
 }
 
+// Local index of node r in each of its incident elements (after the lists are sorted).
+__global__ void k_inc_local(const int32_t* __restrict__ conn, int nen, const int64_t* __restrict__ inc_ptr,
+                            const int32_t* __restrict__ inc_elem, int64_t n_node, uint8_t* __restrict__ inc_local) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_node; r += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t t = inc_ptr[r]; t < inc_ptr[r + 1]; ++t) {
+      const int32_t* ce = conn + (int64_t)inc_elem[t] * nen;
+      int a = 0;
+      while (a < nen - 1 && ce[a] != r) ++a;
+      inc_local[t] = (uint8_t)a;
+    }
+}
+
 // Longest row: max of the row counts, into *out (zeroed by the caller).
 __global__ void k_maxlen(const int32_t* __restrict__ rowcnt, int64_t n, int32_t* out) {
   int32_t m = 0;
@@ -384,6 +396,7 @@ static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, 
   a.em = nullptr;
   a.inc_ptr = p->inc_ptr;
   a.inc_elem = p->inc_elem;
+  a.inc_local = p->inc_local;
   a.n_node = m->n_node;
   a.n_elem = m->n_elem;
   a.nnz = p->nnz;
@@ -524,7 +537,7 @@ fea_status choose_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const v
     if (s1 == FEA_OK && cudaEventRecord(e1, m->stream) != cudaSuccess) s1 = FEA_ERR_CUDA;
     if (s1 == FEA_OK) s1 = fea_sync(m);
     if (s1 == FEA_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) s1 = FEA_ERR_CUDA;
-    if (s1 == FEA_ERR_OOM) continue;  // a candidate that does not fit is skipped
+    if (s1 == FEA_ERR_OOM || s1 == FEA_ERR_TOO_LARGE) continue;  // a candidate that does not fit is skipped
     if (s1 != FEA_OK) {
       status = s1;
       break;
@@ -670,6 +683,7 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->pos);
   cudaFree(p->inc_ptr);
   cudaFree(p->inc_elem);
+  cudaFree(p->inc_local);
   cudaFree(p->ws);
   cudaFree(p->em);
   for (auto& kv : p->cancel) cudaFree(kv.second.first);
@@ -747,6 +761,13 @@ fea_status fea_pattern_build(fea_mesh* m, fea_pattern** out) {
   k_rows<<<rg, ROW_WARPS * 32, smem, s>>>(m->conn, nen, p->inc_ptr, p->inc_elem, N, 1, nullptr, p->rowptr, p->colind,
                                           m->status);
   if (tot > 0) k_posmap<<<grid_for(tot * nen, 256), 256, 0, s>>>(m->conn, E, nen, p->rowptr, p->colind, p->pos);
+  if (cudaMalloc(&p->inc_local, std::max<int64_t>(tot, 1)) != cudaSuccess) {
+    cudaGetLastError();
+    return done(fail(FEA_ERR_OOM, "device allocation of the incidence index failed"));
+  }
+  if (N > 0)
+    k_inc_local<<<(unsigned)std::min<int64_t>(grid_for(N, 256), 152 * 16), 256, 0, s>>>(m->conn, nen, p->inc_ptr,
+                                                                                         p->inc_elem, N, p->inc_local);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return done(fail(FEA_ERR_CUDA, "pattern launch: %s", cudaGetErrorString(e)));
   st = fea_sync(m);

@@ -32,6 +32,7 @@ struct GatherArgs {
   const int64_t* rowptr;
   const int64_t* inc_ptr;
   const int32_t* inc_elem;
+  const uint8_t* inc_local;
   float* values;
   float* rhs;
   int64_t n_node, nnz;
@@ -42,6 +43,7 @@ template <int NEN>
 __global__ void __launch_bounds__(GATHER_THREADS) k_gather(GatherArgs g) {
   extern __shared__ __align__(16) float sm_gather[];
   constexpr int64_t ENTRIES = NEN * NEN + NEN;
+  constexpr int K = 16;                         // element-row values in flight per lane
   float* acc = sm_gather;                       // [n_eq][accs]
   float* racc = sm_gather + g.n_eq * g.accs;    // [n_eq][raccs]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -49,26 +51,61 @@ __global__ void __launch_bounds__(GATHER_THREADS) k_gather(GatherArgs g) {
   const int64_t r1 = min(g.n_node, r0 + g.rows);
   const int64_t k0 = g.rowptr[r0], k1 = g.rowptr[r1];
   const int nq = g.n_eq;
+  const int per = (NEN + 1) * nq;               // values of one element row: NEN columns + RHS, all equations
+  const int J = max(1, min(32, (32 * K) / per));  // elements whose values are loaded before any is added
+  // this lane's values of a load round: flat index f = lane + 32 i = jj * per + b * nq + q
+  // (b == NEN: the RHS entry), packed as jj | b << 8 | q << 16, or -1 past the round
+  int code[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    const int f = lane + 32 * i, jj = f / per, rem = f - jj * per, b = rem / nq;
+    code[i] = jj < J ? jj | (b << 8) | ((rem - b * nq) << 16) : -1;
+  }
   for (int i = threadIdx.x; i < nq * (g.accs + g.raccs); i += GATHER_THREADS) sm_gather[i] = 0.f;
   __syncthreads();
 
   for (int64_t r = r0 + warp; r < r1; r += GATHER_THREADS / 32) {
-    float* rrow = racc + (r - r0);
-    for (int64_t t = g.inc_ptr[r]; t < g.inc_ptr[r + 1]; ++t) {
-      const int64_t e = g.inc_elem[t];
-      // local index of node r in element e
-      const int32_t cn = lane < NEN ? g.conn[e * NEN + lane] : -1;
-      const unsigned hit = __ballot_sync(0xffffffffu, (int64_t)cn == r);
-      const int a = __ffs(hit) - 1;
-      const float* src = g.em + (e * ENTRIES + (int64_t)a * NEN) * nq;
-      const int32_t* pe = g.pos + (e * NEN + a) * NEN;
-      for (int idx = lane; idx < NEN * nq; idx += 32) {
-        const int b = idx / nq, q = idx - b * nq;
-        acc[q * g.accs + (int)(pe[b] - k0)] += __ldcs(src + idx);  // read once: evict first
+    const int64_t t0 = g.inc_ptr[r];
+    const int m = (int)(g.inc_ptr[r + 1] - t0);
+    for (int j0 = 0; j0 < m; j0 += 32) {
+      // lane l holds incident element j0 + l and the row's local index in it
+      int64_t e_l = 0;
+      int a_l = 0;
+      if (j0 + lane < m) {
+        e_l = g.inc_elem[t0 + j0 + lane];
+        a_l = g.inc_local[t0 + j0 + lane];
       }
-      const float* srb = g.em + (e * ENTRIES + NEN * NEN + a) * nq;
-      for (int q = lane; q < nq; q += 32) rrow[q * g.raccs] += __ldcs(srb + q);
-      __syncwarp();  // the next element's lanes may update the words this one just wrote
+      const int mj = min(32, m - j0);
+      for (int jb = 0; jb < mj; jb += J) {
+        const int nj = min(J, mj - jb);
+        // flat index f = jj * per + b * nq + q (b == NEN: the RHS entry): lane takes f = lane + 32 i
+        float val[K];
+        int dst[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+          dst[i] = -1;
+          val[i] = 0.f;
+          const int jj = code[i] & 0xff, b = (code[i] >> 8) & 0xff, q = code[i] >> 16;
+          const int64_t e = __shfl_sync(0xffffffffu, e_l, min(jb + jj, 31));
+          const int a = __shfl_sync(0xffffffffu, a_l, min(jb + jj, 31));
+          if (code[i] >= 0 && jj < nj) {
+            if (b < NEN) {
+              val[i] = __ldcs(g.em + (e * ENTRIES + (int64_t)a * NEN + b) * nq + q);
+              dst[i] = q * g.accs + (int)(g.pos[(e * NEN + a) * NEN + b] - k0);
+            } else {
+              val[i] = __ldcs(g.em + (e * ENTRIES + NEN * NEN + a) * nq + q);
+              dst[i] = nq * g.accs + q * g.raccs + (int)(r - r0);
+            }
+          }
+        }
+        // add element by element: within one element the words are distinct
+        for (int jj = 0; jj < nj; ++jj) {
+#pragma unroll
+          for (int i = 0; i < K; ++i)
+            if (dst[i] >= 0 && (code[i] & 0xff) == jj) sm_gather[dst[i]] += val[i];
+          __syncwarp();
+        }
+      }
     }
   }
   __syncthreads();
@@ -93,6 +130,8 @@ template <int NEN>
 fea_status launch_t(const GatherArgs& g0, int maxcol, cudaStream_t s) {
   GatherArgs g = g0;
   // rows per CTA: every row of the CTA must fit, R rows of at most maxcol entries each
+  if ((int64_t)g.n_eq * (NEN + 1) > 32 * 16)
+    return fail(FEA_ERR_TOO_LARGE, "gather: %d equations x %d columns exceed one load round", g.n_eq, NEN + 1);
   const size_t per_row = sizeof(float) * (size_t)g.n_eq * ((size_t)std::max(maxcol, 1) + 1);
   int rows = (int)std::max<size_t>(1, GATHER_SMEM_TARGET / per_row);
   rows = std::min(rows, 1024);
@@ -131,6 +170,7 @@ fea_status launch_gather_f32(const AsmArgs<float>& a, fea_elem_t type, int maxco
   g.rowptr = a.rowptr;
   g.inc_ptr = a.inc_ptr;
   g.inc_elem = a.inc_elem;
+  g.inc_local = a.inc_local;
   g.values = a.values;
   g.rhs = a.rhs;
   g.n_node = a.n_node;

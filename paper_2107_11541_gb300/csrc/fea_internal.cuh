@@ -79,6 +79,7 @@ struct fea_pattern {
   int32_t* pos;        // [n_elem][nen][nen]
   int64_t* inc_ptr;    // [n_node+1] node -> element incidence
   int32_t* inc_elem;   // [nen*n_elem]
+  uint8_t* inc_local;  // [nen*n_elem] local index of the node in each incident element
   fea_rowowned_plan* plan;  // may be null (row-owned path unavailable for this mesh)
   int32_t maxcol;      // longest row
   // element-matrix scratch of the gather scatter, grown on demand
@@ -226,6 +227,7 @@ struct AsmArgs {
                    // (written instead of the atomic adds); null otherwise
   const int64_t* inc_ptr;   // [n_node+1] node -> incident elements
   const int32_t* inc_elem;  // ascending element ids per node
+  const uint8_t* inc_local; // local index of the node in each incident element
   int64_t n_node;
   int64_t n_elem;
   int64_t nnz;

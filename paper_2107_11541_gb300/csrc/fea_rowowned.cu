@@ -228,6 +228,15 @@ struct Builder {
       live -= (int)flushing.size();
       flushing.swap(completed);
       completed.clear();
+      {  // the batch's completed rows in row order: consecutive records are adjacent CSR rows
+        const size_t f0 = (size_t)batch_flush.back() * 4, nf = flush_meta.size() / 4 - (size_t)batch_flush.back();
+        std::vector<std::array<int32_t, 4>> recs(nf);
+        for (size_t i = 0; i < nf; ++i)
+          for (int c = 0; c < 4; ++c) recs[i][c] = flush_meta[f0 + 4 * i + c];
+        std::sort(recs.begin(), recs.end());
+        for (size_t i = 0; i < nf; ++i)
+          for (int c = 0; c < 4; ++c) flush_meta[f0 + 4 * i + c] = recs[i][c];
+      }
       batch_visit.push_back((int32_t)visits());
       batch_flush.push_back((int32_t)flushes());
     }
@@ -344,10 +353,12 @@ static fea_status build_variant(fea_rowowned_plan* P, int n_eq, Variant* v) {
     }
   double vol = std::max(1e-300, (hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]));
   double spacing = std::cbrt(vol / std::max<int64_t>(1, E));  // hex cell width
-  int cols = std::max(1, (int)(0.45 * n_slots));             // node columns per tile (two planes live)
+  // node columns per tile: two planes live plus the slots still being written out; 0.35 of the
+  // slots measured best on Hex8 128^3 (0.25-0.55 swept: fuller tiles cut the halo but leave
+  // fewer, larger units to balance over the CTAs)
+  int cols = std::max(1, (int)(0.35 * n_slots));
   // tiles about 3x wider in x (the fastest node-id direction) than in y: the rows a batch
-  // completes then form longer runs of consecutive CSR rows, which HBM writes much faster,
-  // for about the same halo as a square tile of the same area
+  // completes form runs of consecutive CSR rows (measured a few percent faster than square)
   const double aspect = 3.0;
   int tx0 = std::max(1, (int)std::floor(std::sqrt((double)cols * aspect)));
   int ty0 = std::max(1, cols / tx0);

@@ -112,19 +112,21 @@ __device__ __forceinline__ void stage_nodes(const RoArgs& r, int t, const Stage&
   }
 }
 
-// Writes the rows completed by batch tb to HBM and clears their slots; warp w of nw takes
-// rows w, w + nw, ...  Per row the lanes walk its (equation, column) values with the
-// column fastest (column index len is the RHS entry), so each equation's segment is
-// stored contiguously.  The warp reads 32 flush records at a time, one per lane.
+// Writes the rows completed by batch tb to HBM and clears their slots; warp w of nw takes a
+// contiguous share of the batch's records, which the plan sorts by row, so that a warp's
+// consecutive stores of one equation land on adjacent CSR rows.  Per row the lanes walk its
+// (equation, column) values with the column fastest (column index len is the RHS entry), so
+// each equation's segment is stored contiguously.  The warp reads 32 flush records at a
+// time, one per lane.
 __device__ __forceinline__ void flush_rows(const RoArgs& r, float* win, int tb, int w0, int nw) {
   const AsmArgs<float>& A_ = r.a;
   const int lane = threadIdx.x & 31, n_eq = A_.eq_count;
-  const int f0 = r.batch_flush[tb], nf = r.batch_flush[tb + 1] - f0;
+  const int fb = r.batch_flush[tb], nb = r.batch_flush[tb + 1] - fb;
+  const int f0 = fb + (int)(((int64_t)nb * w0) / nw), nf = fb + (int)(((int64_t)nb * (w0 + 1)) / nw) - f0;
   int4 rec = make_int4(0, 0, 0, 0);
-  for (int f = w0, j = 32; f < nf; f += nw, ++j) {
-    if (j == 32) {  // records f, f + nw, ..., f + 31 nw
-      const int fl = f + lane * nw;
-      if (fl < nf) rec = __ldg(r.flush_meta + f0 + fl);
+  for (int f = 0, j = 32; f < nf; ++f, ++j) {
+    if (j == 32) {  // records f .. f + 31
+      if (f + lane < nf) rec = __ldg(r.flush_meta + f0 + f + lane);
       j = 0;
     }
     const int4 m = make_int4(__shfl_sync(0xffffffffu, rec.x, j), __shfl_sync(0xffffffffu, rec.y, j),
@@ -149,8 +151,8 @@ __device__ __forceinline__ void flush_rows(const RoArgs& r, float* win, int tb, 
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             if (q0 + k >= n_eq) break;
-            if (lane < len) __stcs(dv + (int64_t)(q0 + k) * A_.nnz, v[k]);
-            else __stcs(dr + (int64_t)(q0 + k) * A_.n_node, v[k]);
+            if (lane < len) dv[(int64_t)(q0 + k) * A_.nnz] = v[k];
+            else dr[(int64_t)(q0 + k) * A_.n_node] = v[k];
           }
         }
       }
@@ -160,7 +162,7 @@ __device__ __forceinline__ void flush_rows(const RoArgs& r, float* win, int tb, 
         const float v = win[(base + (c < len ? c : r.maxcol)) * r.neqs + q];
         float* dst = c < len ? A_.values + (int64_t)(A_.eq0 + q) * A_.nnz + k0 + c
                              : A_.rhs + (int64_t)(A_.eq0 + q) * A_.n_node + row;
-        __stcs(dst, v);  // streaming store: written once, not re-read by this kernel
+        *dst = v;  // plain store: the L2 keeps the line until its neighbour row completes it
         q += step_q;
         c += step_c;
         if (c >= w) {
