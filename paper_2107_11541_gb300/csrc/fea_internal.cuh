@@ -245,6 +245,9 @@ fea_status launch_generic_f64(const AsmArgs<double>& a, fea_elem_t type, cudaStr
 fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s);
 // FP32 Tet4: one thread per (element, equation) (atomics, or the gather scratch if a.em).
 fea_status launch_tet4_f32(const AsmArgs<float>& a, cudaStream_t s);
+// FP32 Hex27, one CTA per element, full operator and up to 12 equations (hex27_kernel_applies).
+bool hex27_kernel_applies(const AsmArgs<float>& a);
+fea_status launch_hex27_f32(const AsmArgs<float>& a, cudaStream_t s);
 // Row gather of the element matrices in a.em into a.values / a.rhs (overwrite or add).
 fea_status launch_gather_f32(const AsmArgs<float>& a, fea_elem_t type, int maxcol, bool accumulate, cudaStream_t s);
 // Bytes of element-matrix scratch the gather scatter needs.
