@@ -550,15 +550,20 @@ fea_status choose_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const v
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (status != FEA_OK) return status;
-  // keep the winner's resources only
-  if (best.scatter == FEA_SCATTER_ROWOWNED) plan_trim(p->plan, plan_group_size(n_eq, best.groups));
-  else plan_trim(p->plan, -1);
-  if (best.scatter != FEA_SCATTER_GATHER) {
+  // keep the resources of the winners (this equation count's and those tuned before) only
+  p->tuned[n_eq] = std::make_pair(best.scatter, best.groups);
+  std::vector<int> keep;
+  bool any_gather = false;
+  for (const auto& kv : p->tuned) {
+    if (kv.second.first == FEA_SCATTER_ROWOWNED) keep.push_back(plan_group_size(kv.first, kv.second.second));
+    any_gather |= kv.second.first == FEA_SCATTER_GATHER;
+  }
+  plan_trim(p->plan, keep);
+  if (!any_gather) {
     cudaFree(p->em);
     p->em = nullptr;
     p->em_bytes = 0;
   }
-  p->tuned[n_eq] = std::make_pair(best.scatter, best.groups);
   *out = best;
   return FEA_OK;
 }
@@ -607,6 +612,10 @@ fea_status fea_mesh_destroy(fea_mesh* m) {
   cudaFree(m->xlo);
   cudaFree(m->conn);
   cudaFree(m->status);
+  if (m->copy_ready) {
+    for (int i = 0; i < fea_mesh::N_COPY; ++i) cudaStreamDestroy(m->copy_stream[i]);
+    for (int i = 0; i <= fea_mesh::N_COPY; ++i) cudaEventDestroy(m->copy_event[i]);
+  }
   delete m;
   return FEA_OK;
 }
@@ -855,17 +864,66 @@ fea_status fea_assemble_host(fea_mesh* m, const fea_pattern* cp, const void* vel
   char* d_phi = d_sr + al(b_f);
   char* d_val = d_phi + al(b_f);
   char* d_rhs = d_val + al(b_val);
-  FEA_CUDA_TRY(cudaMemcpyAsync(d_vel, vel, b_vel, cudaMemcpyHostToDevice, s));
-  FEA_CUDA_TRY(cudaMemcpyAsync(d_kd, kd, b_f, cudaMemcpyHostToDevice, s));
-  FEA_CUDA_TRY(cudaMemcpyAsync(d_sr, sr, b_f, cudaMemcpyHostToDevice, s));
-  FEA_CUDA_TRY(cudaMemcpyAsync(d_phi, phi, b_f, cudaMemcpyHostToDevice, s));
-  if (o.accumulate) {
-    FEA_CUDA_TRY(cudaMemcpyAsync(d_val, values, b_val, cudaMemcpyHostToDevice, s));
-    FEA_CUDA_TRY(cudaMemcpyAsync(d_rhs, rhs, b_f, cudaMemcpyHostToDevice, s));
+  // Copies run on N_COPY side streams at once (one copy engine per stream), ordered against
+  // the assembly on the mesh stream by events: several concurrent copies move host data
+  // faster than one.
+  constexpr int NC = fea_mesh::N_COPY;
+  if (!m->copy_ready) {
+    for (int i = 0; i < NC; ++i) FEA_CUDA_TRY(cudaStreamCreateWithFlags(&m->copy_stream[i], cudaStreamNonBlocking));
+    for (int i = 0; i <= NC; ++i) FEA_CUDA_TRY(cudaEventCreateWithFlags(&m->copy_event[i], cudaEventDisableTiming));
+    m->copy_ready = true;
   }
-  FEA_TRY(fea_assemble(m, p, d_vel, d_kd, d_sr, d_phi, dt, n_eq, &o, d_val, d_rhs));
-  FEA_CUDA_TRY(cudaMemcpyAsync(values, d_val, b_val, cudaMemcpyDeviceToHost, s));
-  FEA_CUDA_TRY(cudaMemcpyAsync(rhs, d_rhs, b_f, cudaMemcpyDeviceToHost, s));
+  cudaEvent_t start = m->copy_event[NC];  // recorded on s before each batch of copies
+  struct Copy { void* dst; const void* src; size_t bytes; };
+  // copies after the work on s so far; join = s waits for them (else join_copies does later)
+  auto join_copies = [&]() -> fea_status {
+    for (int i = 0; i < NC; ++i) {
+      FEA_CUDA_TRY(cudaEventRecord(m->copy_event[i], m->copy_stream[i]));
+      FEA_CUDA_TRY(cudaStreamWaitEvent(s, m->copy_event[i], 0));
+    }
+    return FEA_OK;
+  };
+  auto run_copies = [&](const Copy* c, int n, cudaMemcpyKind kind, bool join) -> fea_status {
+    FEA_CUDA_TRY(cudaEventRecord(start, s));
+    for (int i = 0; i < NC; ++i) FEA_CUDA_TRY(cudaStreamWaitEvent(m->copy_stream[i], start, 0));
+    for (int i = 0; i < n; ++i)
+      if (c[i].bytes) FEA_CUDA_TRY(cudaMemcpyAsync(c[i].dst, c[i].src, c[i].bytes, kind, m->copy_stream[i % NC]));
+    return join ? join_copies() : FEA_OK;
+  };
+  // large arrays in NC pieces, cut at 256-byte boundaries
+  auto split = [&](Copy* out, int& n, char* d, const char* h, size_t bytes, bool to_dev) {
+    const size_t piece = ((bytes + NC - 1) / NC + 255) & ~(size_t)255;
+    for (size_t off = 0; off < bytes; off += piece) {
+      const size_t b = std::min(piece, bytes - off);
+      out[n++] = to_dev ? Copy{d + off, h + off, b} : Copy{(void*)(h + off), d + off, b};
+    }
+  };
+  Copy in[4 + 2 * NC];
+  int n_in = 0;
+  in[n_in++] = Copy{d_vel, vel, b_vel};
+  in[n_in++] = Copy{d_kd, kd, b_f};
+  in[n_in++] = Copy{d_sr, sr, b_f};
+  in[n_in++] = Copy{d_phi, phi, b_f};
+  if (o.accumulate) {
+    split(in, n_in, d_val, (const char*)values, b_val, true);
+    in[n_in++] = Copy{d_rhs, rhs, b_f};
+  }
+  FEA_TRY(run_copies(in, n_in, cudaMemcpyHostToDevice, true));
+  // Large outputs: the equations are assembled in parts, each an independent assembly of its
+  // slices, so that part k's values travel back while part k+1 computes.
+  const int parts = (b_val > ((size_t)256 << 20) && n_eq >= 3) ? 3 : 1;  // 3 measured best of 3 and 6
+  const int per = (n_eq + parts - 1) / parts;
+  for (int q0 = 0; q0 < n_eq; q0 += per) {
+    const int cnt = std::min(per, n_eq - q0);
+    const size_t fo = es * (size_t)q0 * N, vo = es * (size_t)q0 * nnz;
+    FEA_TRY(fea_assemble(m, p, d_vel, d_kd + fo, d_sr + fo, d_phi + fo, dt, cnt, &o, d_val + vo, d_rhs + fo));
+    Copy outc[2 * NC + 1];
+    int n_out = 0;
+    split(outc, n_out, d_val + vo, (const char*)values + vo, es * (size_t)cnt * nnz, false);
+    outc[n_out++] = Copy{(char*)rhs + fo, d_rhs + fo, es * (size_t)cnt * N};
+    FEA_TRY(run_copies(outc, n_out, cudaMemcpyDeviceToHost, false));  // overlaps the next part
+  }
+  FEA_TRY(join_copies());
   return fea_sync(m);
 }
 

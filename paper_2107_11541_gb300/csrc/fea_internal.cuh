@@ -67,6 +67,11 @@ struct fea_mesh {
   float* xlo;         // [3][n_node] low part: coordinate - hi, rounded to float
   int32_t* conn;      // [n_elem][nen]
   uint32_t* status;   // device status word
+  // fea_assemble_host: side streams and events for concurrent host<->device copies
+  static constexpr int N_COPY = 4;
+  cudaStream_t copy_stream[N_COPY];
+  cudaEvent_t copy_event[N_COPY + 1];
+  bool copy_ready;
 };
 
 struct fea_rowowned_plan;  // schedules of the row-owned kernels (per element type)

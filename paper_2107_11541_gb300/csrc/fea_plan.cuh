@@ -16,7 +16,7 @@ fea_status plan_prepare(fea_rowowned_plan* plan, int n_eq, bool* ok);
 // (the last one smaller); plan_prepare must have succeeded for that group size.
 fea_status plan_assemble(fea_rowowned_plan* plan, const AsmArgs<float>& a, int accumulate, int groups, cudaStream_t s);
 int plan_group_size(int n_eq, int groups);
-// Frees the schedules of every group size but keep_n_eq.
-void plan_trim(fea_rowowned_plan* plan, int keep_n_eq);
+// Frees the schedules of every group size not listed in keep.
+void plan_trim(fea_rowowned_plan* plan, const std::vector<int>& keep);
 
 }  // namespace fea

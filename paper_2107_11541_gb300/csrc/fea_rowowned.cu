@@ -486,11 +486,11 @@ __global__ void k_fields_nodemajor(const float* __restrict__ kd, const float* __
 
 int plan_group_size(int n_eq, int groups) { return (n_eq + groups - 1) / groups; }
 
-void plan_trim(fea_rowowned_plan* P, int keep_n_eq) {
+void plan_trim(fea_rowowned_plan* P, const std::vector<int>& keep) {
   if (!P) return;
   std::lock_guard<std::mutex> lk(P->mu);
   for (auto it = P->variants.begin(); it != P->variants.end();) {
-    if (it->first != keep_n_eq) {
+    if (std::find(keep.begin(), keep.end(), it->first) == keep.end()) {
       ro::free_variant(it->second);
       it = P->variants.erase(it);
     } else {

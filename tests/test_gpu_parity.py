@@ -98,6 +98,12 @@ def test_host_entry_point(case):
     import torch
     ea, eb = compare_full(run, w.fields, fea.FEA_F32_FUSED, values=torch.from_numpy(vals), rhs=torch.from_numpy(rhs))
     assert ea <= TOL_F32 and eb <= TOL_F32
+    # accumulate through the host entry point: the outputs are copied in, added to and copied back
+    v2, r2 = vals.copy(), rhs.copy()
+    fea.fea_assemble_host(run.handle, run.pattern, f.velocity, f.diffusivity, f.reaction, f.phi_old, f.dt, q,
+                          fea.fea_default_opts(accumulate=1), v2, r2)
+    assert np.abs(v2 - 2 * vals).max() <= 1e-6 * np.abs(vals).max()
+    assert np.abs(r2 - 2 * rhs).max() <= 1e-6 * np.abs(rhs).max()
 
 
 def test_unused_nodes_and_subset():
