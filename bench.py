@@ -228,6 +228,8 @@ def main():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cells", type=int, default=None, help="shrink to this many cells per axis (profiling)")
+    ap.add_argument("--residual", action="store_true",
+                    help="also time the matrix-free residual r = b - A phi (fea_residual) on the same workload")
     ap.add_argument("--graph", type=int, default=None,
                     help="1: time the K steps as one CUDA graph of K (assemble, field update) time steps "
                          "(default on for hex8_256_32eq)")
@@ -374,6 +376,20 @@ def main():
 
     if rank == 0 and not args.no_parity:
         out["parity"] = sampled_parity(w, values, rhs, p, nnz)
+    if args.residual:
+        r = torch.empty((q, m.n_node), dtype=torch.float32, device="cuda")
+        ro = fea.fea_default_opts()
+        fea.fea_residual(h, p, *dev, dev[3], fld.dt, q, ro, r)
+        ra, rb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ra.record(stream)
+        for _ in range(3):
+            fea.fea_residual(h, p, *dev, dev[3], fld.dt, q, ro, r)
+        rb.record(stream)
+        torch.cuda.synchronize()
+        rms = ra.elapsed_time(rb) / 3
+        out["residual"] = {"ms_per_step": rms, "value": m.n_elem * q / (rms * 1e-3), "unit": UNIT,
+                           "what": "matrix-free r = b - A phi_old, FP32"}
+        del r
 
     if not args.no_f64 and rank == 0:
         q64 = q if m.n_elem * q <= 60_000_000 else 4

@@ -170,6 +170,22 @@ FEA_API fea_status fea_assemble(fea_mesh* mesh, const fea_pattern* pattern, cons
                         int32_t n_eq, const fea_assemble_opts* opts, void* values, void* rhs);
 
 /*
+ * fea_residual -- the matrix-free residual of the same discretisation at a field phi:
+ *     r[q][n] = b_q[n] - sum_e (A^e_q phi^e_q)[n]
+ * formed element by element without building the CSR matrix (an explicit step applies the
+ * operator rather than solving with it, Sec. 2).  A^e and b^e are exactly the element
+ * contributions fea_assemble sums, so r = rhs - values * phi up to rounding.
+ *   velocity, diffusivity, reaction, phi_old: as in fea_assemble
+ *   phi  [n_eq][n_node] the field the operator is applied to
+ *   r    [n_eq][n_node] output (opts->accumulate = 1 adds to it)
+ * Precision and term mask from opts; the scatter option is ignored (atomic adds into the
+ * zeroed r).  Device arrays, enqueued on the mesh's stream.
+ */
+FEA_API fea_status fea_residual(fea_mesh* mesh, const fea_pattern* pattern, const void* velocity,
+                                const void* diffusivity, const void* reaction, const void* phi_old, const void* phi,
+                                double dt, int32_t n_eq, const fea_assemble_opts* opts, void* r);
+
+/*
  * fea_assemble_host -- the same operation on HOST arrays (same shapes and
  * types as fea_assemble).  Copies the inputs to a device workspace owned by the
  * pattern, assembles, copies values and rhs back, and waits for completion.

@@ -397,6 +397,8 @@ static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, 
   a.inc_ptr = p->inc_ptr;
   a.inc_elem = p->inc_elem;
   a.inc_local = p->inc_local;
+  a.phi_eval = nullptr;
+  a.resid = nullptr;
   a.n_node = m->n_node;
   a.n_elem = m->n_elem;
   a.nnz = p->nnz;
@@ -816,6 +818,39 @@ fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, cons
   }
   FEA_TRY(cancel_fix_rows(a, m->type, p->maxcol, it->second.first, it->second.second, m->stream));
   if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, m->stream));
+  return FEA_OK;
+}
+
+fea_status fea_residual(fea_mesh* m, const fea_pattern* p, const void* vel, const void* kd, const void* sr,
+                        const void* phi_old, const void* phi, double dt, int32_t n_eq, const fea_assemble_opts* opts,
+                        void* r) {
+  fea_assemble_opts o;
+  if (opts) o = *opts;
+  else fea_default_opts(&o);
+  FEA_TRY(check_assemble_args(m, p, vel, kd, sr, phi_old, dt, n_eq, &o, r, r));
+  if (!phi) return fail(FEA_ERR_ARG, "fea_residual: phi is null");
+  cudaStream_t s = m->stream;
+  const size_t es = o.precision == FEA_F64_PLAIN ? sizeof(double) : sizeof(float);
+  if (!o.accumulate) FEA_CUDA_TRY(cudaMemsetAsync(r, 0, es * (size_t)n_eq * (size_t)m->n_node, s));
+  if (o.event_begin) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_begin, s));
+  if (m->n_elem > 0) {
+    if (o.precision == FEA_F64_PLAIN) {
+      AsmArgs<double> a = make_args<double>(m, p, vel, kd, sr, phi_old, dt, n_eq, &o, nullptr, nullptr);
+      a.phi_eval = (const double*)phi;
+      a.resid = (double*)r;
+      for (int q = 0; q < n_eq; ++q) {
+        a.eq0 = q;
+        a.eq_count = 1;
+        FEA_TRY(launch_generic_f64(a, m->type, s));
+      }
+    } else {
+      AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi_old, dt, n_eq, &o, nullptr, nullptr);
+      a.phi_eval = (const float*)phi;
+      a.resid = (float*)r;
+      FEA_TRY(launch_generic_f32(a, m->type, s));
+    }
+  }
+  if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, s));
   return FEA_OK;
 }
 

@@ -39,6 +39,16 @@ __global__ void __launch_bounds__(WARPS * 32) k_generic(AsmArgs<T> p) {
     const T h = warp_geometry<T, T, TYPE>(p, e, S, Nt, lane);
     for (int q = p.eq0; q < p.eq0 + p.eq_count; ++q) {
       warp_coeffs<T, T, TYPE>(p, q, S, Nt, lane, h);
+      if (p.resid) {  // matrix-free: lane a forms row a of A^e and adds b_a - (A^e phi)_a
+        const T* fq = p.phi_eval + (int64_t)q * p.n_node;
+        for (int a = lane; a < NEN; a += 32) {
+          T y = element_rhs<T, TYPE>(S, Nt, a, inv_dt, p.terms);
+          for (int b = 0; b < NEN; ++b) y -= element_entry<T, TYPE>(S, Nt, a, b, inv_dt, p.terms) * fq[node[b]];
+          atomic_add(p.resid + (int64_t)q * p.n_node + node[a], y);
+        }
+        __syncwarp();
+        continue;
+      }
       T* vq = p.values + (int64_t)q * p.nnz;
       const int32_t* pe = p.pos + e * NEN * NEN;
       for (int idx = lane; idx < NEN * NEN; idx += 32) {
@@ -91,6 +101,7 @@ fea_status launch_generic_f64(const AsmArgs<double>& a, fea_elem_t type, cudaStr
 fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s) {
   if (type == FEA_TET4) return launch_tet4_f32(a, s);  // constant gradients: one thread per item
   if (type == FEA_HEX27 && hex27_kernel_applies(a)) return launch_hex27_f32(a, s);  // one CTA per element
+  // (the Hex27 CTA kernel covers the residual mode too)
   return launch_any(a, type, s);
 }
 

@@ -350,7 +350,16 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
     }
     __syncthreads();
     // 5. out
-    if (EM) {
+    if (p.resid) {  // matrix-free: b_a - sum_b A_ab phi_b, one thread per (q, a)
+      for (int i = tid; i < Q * NN; i += H27_THREADS) {
+        const int q = i / NN, a = i - q * NN;
+        const float* fq = p.phi_eval + (int64_t)(p.eq0 + q) * N;
+        const float* Ra = R + q * ENT + a * NN;
+        float y = R[q * ENT + NN * NN + a];
+        for (int b = 0; b < NN; ++b) y = fmaf(-Ra[b], fq[ce[b]], y);
+        atomicAdd(p.resid + (int64_t)(p.eq0 + q) * N + ce[a], y);
+      }
+    } else if (EM) {
       float* dst = p.em + e * ENT * Q;
       for (int i = tid; i < ENT * Q; i += H27_THREADS) {
         const int ent = (int)(((float)i + 0.5f) * invQ), q = i - ent * Q;

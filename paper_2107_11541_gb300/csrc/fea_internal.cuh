@@ -233,6 +233,9 @@ struct AsmArgs {
   const int64_t* inc_ptr;   // [n_node+1] node -> incident elements
   const int32_t* inc_elem;  // ascending element ids per node
   const uint8_t* inc_local; // local index of the node in each incident element
+  // matrix-free residual mode (resid != null): resid[q][n] += b^e_a - (A^e phi)_a, no CSR output
+  const T* phi_eval;        // [n_eq][N] the field A is applied to
+  T* resid;                 // [n_eq][N]
   int64_t n_node;
   int64_t n_elem;
   int64_t nnz;

@@ -136,7 +136,19 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
         for (int c = 0; c < 4; ++c)
           A[a][c] = fmaf(kd_sum, gr[a][0] * gr[c][0] + gr[a][1] * gr[c][1] + gr[a][2] * gr[c][2], A[a][c]);
     }
-    if (p.em) {
+    if (p.resid) {  // matrix-free: b_a - (A^e phi)_a
+      const float* fq = p.phi_eval + fo;
+      float ph[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) ph[c] = __ldg(fq + n[c]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        float y = b[a];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) y = fmaf(-A[a][c], ph[c], y);
+        atomicAdd(p.resid + fo + n[a], y);
+      }
+    } else if (p.em) {
       float* d = p.em + e * 20 * p.eq_count + qq;
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
