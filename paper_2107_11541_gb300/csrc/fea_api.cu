@@ -423,6 +423,13 @@ struct Strategy {
   int groups;   // equation groups of the row-owned scatter
 };
 
+// FP32 element-parallel launch: the batched Hex8 kernel where the mesh has one, else the
+// per-type kernels behind launch_generic_f32.
+fea_status elem_f32(fea_mesh* m, const fea_pattern* p, const AsmArgs<float>& a, cudaStream_t s) {
+  if (m->type == FEA_HEX8 && p->plan) return plan_elem(p->plan, a, s);
+  return launch_generic_f32(a, m->type, s);
+}
+
 bool stream_capturing(cudaStream_t s) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
@@ -476,10 +483,10 @@ fea_status run_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const void
         FEA_TRY(plan_assemble(p->plan, a, o.accumulate, st.groups, s));
       } else if (gather) {
         a.em = (float*)p->em;
-        FEA_TRY(launch_generic_f32(a, m->type, s));
+        FEA_TRY(elem_f32(m, p, a, s));
         FEA_TRY(launch_gather_f32(a, m->type, p->maxcol, o.accumulate != 0, s));
       } else {
-        FEA_TRY(launch_generic_f32(a, m->type, s));
+        FEA_TRY(elem_f32(m, p, a, s));
       }
     }
   }
@@ -847,7 +854,7 @@ fea_status fea_residual(fea_mesh* m, const fea_pattern* p, const void* vel, cons
       AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi_old, dt, n_eq, &o, nullptr, nullptr);
       a.phi_eval = (const float*)phi;
       a.resid = (float*)r;
-      FEA_TRY(launch_generic_f32(a, m->type, s));
+      FEA_TRY(elem_f32(m, p, a, s));
     }
   }
   if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, s));

@@ -16,6 +16,9 @@ fea_status plan_prepare(fea_rowowned_plan* plan, int n_eq, bool* ok);
 // (the last one smaller); plan_prepare must have succeeded for that group size.
 fea_status plan_assemble(fea_rowowned_plan* plan, const AsmArgs<float>& a, int accumulate, int groups, cudaStream_t s);
 int plan_group_size(int n_eq, int groups);
+// Element-parallel FP32 Hex8 (no schedule): atomics, the gather scratch (a.em) or the
+// matrix-free residual (a.resid), for the launch's equations.
+fea_status plan_elem(fea_rowowned_plan* plan, const AsmArgs<float>& a, cudaStream_t s);
 // Frees the schedules of every group size not listed in keep.
 void plan_trim(fea_rowowned_plan* plan, const std::vector<int>& keep);
 

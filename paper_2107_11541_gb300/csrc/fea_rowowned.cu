@@ -86,6 +86,8 @@ struct fea_rowowned_plan {
   std::vector<double> coords;
   std::vector<int64_t> rowptr, inc_ptr;
   std::vector<int32_t> colind, inc_elem;
+  float* elem_fnode = nullptr;  // node-major fields for the element-parallel kernel
+  size_t elem_fnode_bytes = 0;
 };
 
 namespace fea {
@@ -436,6 +438,7 @@ fea_status plan_build(fea_mesh* m, fea_pattern* p, fea_rowowned_plan** out) {
 void plan_destroy(fea_rowowned_plan* P) {
   if (!P) return;
   for (auto& kv : P->variants) ro::free_variant(kv.second);
+  cudaFree(P->elem_fnode);
   delete P;
 }
 
@@ -535,6 +538,54 @@ static fea_status assemble_group(ro::Variant* v, const AsmArgs<float>& a, int ac
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   unsigned grid = (unsigned)std::max(1, std::min(v->n_units, nsm));
   kern<<<grid, ro::THREADS, v->smem, s>>>(r);
+  FEA_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return FEA_OK;
+}
+
+fea_status plan_elem(fea_rowowned_plan* P, const AsmArgs<float>& a, cudaStream_t s) {
+  // node-major fields of all the launch's equations, in a scratch owned by the plan
+  const int rec = 3 * a.eq_count + 3;
+  const size_t need = sizeof(float) * (size_t)a.n_node * rec;
+  if (P->elem_fnode_bytes < need) {
+    FEA_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(P->elem_fnode);
+    P->elem_fnode = nullptr;
+    P->elem_fnode_bytes = 0;
+    if (cudaMalloc(&P->elem_fnode, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(FEA_ERR_OOM, "element kernel: %zu bytes of node-major fields", need);
+    }
+    P->elem_fnode_bytes = need;
+  }
+  const int64_t fo = (int64_t)a.eq0 * a.n_node;
+  {
+    const size_t tsm = sizeof(float) * rec * 33;
+    FEA_CUDA_TRY(cudaFuncSetAttribute(ro::k_fields_nodemajor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+    ro::k_fields_nodemajor<<<(unsigned)((a.n_node + 31) / 32), 256, tsm, s>>>(a.kd + fo, a.sr + fo, a.phi + fo, a.vel,
+                                                                              a.n_node, a.eq_count, P->elem_fnode);
+    FEA_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+  }
+  ro::RoArgs r{};
+  r.a = a;
+  r.fnode = P->elem_fnode;
+  r.rec = rec;
+  r.be = ro::batch_elems(a.eq_count);
+  const size_t smem = sizeof(float) * (size_t)r.be * (ro::GEO_ELEM + ro::NEN * ro::RAW + ro::NEN);
+  const bool full = a.terms == FEA_TERM_ALL;
+  auto pick = [&](auto full_k, auto part_k) { return full ? full_k : part_k; };
+  void (*kern)(ro::RoArgs) =
+      a.resid ? pick(ro::k_hex8_elem<true, ro::EMODE_RESIDUAL>, ro::k_hex8_elem<false, ro::EMODE_RESIDUAL>)
+      : a.em  ? pick(ro::k_hex8_elem<true, ro::EMODE_SCRATCH>, ro::k_hex8_elem<false, ro::EMODE_SCRATCH>)
+              : pick(ro::k_hex8_elem<true, ro::EMODE_ATOMIC>, ro::k_hex8_elem<false, ro::EMODE_ATOMIC>);
+  FEA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nb = (a.n_elem + r.be - 1) / r.be;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, nsm));
+  if (a.n_elem > 0) kern<<<grid, ro::THREADS, smem, s>>>(r);
   FEA_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return FEA_OK;

@@ -291,6 +291,88 @@ __device__ __forceinline__ void load_fields(const RoArgs& r, const Stage& S, int
   }
 }
 
+// The Gauss-point sums of one (element, equation) item (all Hex8 kernels): the element
+// matrix as the packed product Am and the symmetric diffusion Dm, and the RHS bv2, from the
+// element's geometry Ge (GEO floats per point, then 4/h^2) and the interpolated k, s, phi.
+template <bool FULL>
+__device__ __forceinline__ void item_sums(const float* Ge, float ck, const float kg[NG], const float sg[NG],
+                                          const float pg[NG], float inv_dt, bool t_mass, bool t_conv, bool t_diff,
+                                          bool t_reac, bool t_supg, float2 (&Am)[NEN][NEN / 2], float2 (&Dm)[18],
+                                          float2 (&bv2)[NEN / 2]) {
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const float4* G4 = reinterpret_cast<const float4*>(Ge + g * GEO);
+    float gv[GEO];
+#pragma unroll
+    for (int k2 = 0; k2 < GEO / 4 - 1; ++k2) {
+      const float4 x = G4[k2];
+      gv[4 * k2] = x.x;
+      gv[4 * k2 + 1] = x.y;
+      gv[4 * k2 + 2] = x.z;
+      gv[4 * k2 + 3] = x.w;
+    }
+    {
+      const float4 x = G4[GEO / 4 - 1];
+      gv[GEO - 4] = x.x;
+      gv[GEO - 3] = x.y;
+    }
+    const float dv = gv[0];
+    const float den = fmaf(ck, kg[g], gv[1] + sg[g]);
+    const float tau = den > 0.f ? __fdividef(1.f, den) : 0.f;
+    const float dvt = t_supg ? dv * tau : 0.f;
+    const float sigs = inv_dt + sg[g];
+    float P[NEN], Q[NEN];
+    if (FULL) {
+      // all terms: dV (N_a + tau u.gradN_a)((1/dt + s) N_b + u.gradN_b), one rank-1 product
+#pragma unroll
+      for (int a = 0; a < NEN; ++a) {
+        P[a] = fmaf(dvt, gv[2 + a], dv * hex_n(a, g));
+        Q[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
+      }
+#pragma unroll
+      for (int a = 0; a < NEN; ++a) {
+        const float2 pa = make_float2(P[a], P[a]);
+#pragma unroll
+        for (int b = 0; b < NEN / 2; ++b) Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
+      }
+    } else {
+      // dV N_a (sig N_b + [conv] u.gradN_b) + [supg] dV tau u.gradN_a ((1/dt + s) N_b + u.gradN_b)
+      const float sig = (t_mass ? inv_dt : 0.f) + (t_reac ? sg[g] : 0.f);
+      float Ps[NEN], R[NEN];
+#pragma unroll
+      for (int a = 0; a < NEN; ++a) {
+        P[a] = dv * hex_n(a, g);
+        Ps[a] = dvt * gv[2 + a];
+        Q[a] = sig * hex_n(a, g) + (t_conv ? gv[2 + a] : 0.f);
+        R[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
+      }
+#pragma unroll
+      for (int a = 0; a < NEN; ++a) {
+        const float2 pa = make_float2(P[a], P[a]), ps = make_float2(Ps[a], Ps[a]);
+#pragma unroll
+        for (int b = 0; b < NEN / 2; ++b) {
+          Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
+          Am[a][b] = __ffma2_rn(ps, make_float2(R[2 * b], R[2 * b + 1]), Am[a][b]);
+        }
+      }
+      if (!t_mass) {
+#pragma unroll
+        for (int a = 0; a < NEN; ++a) P[a] = 0.f;
+      }
+#pragma unroll
+      for (int a = 0; a < NEN; ++a) P[a] += Ps[a];
+    }
+    if (t_diff) {
+      const float2 k2v = make_float2(kg[g], kg[g]);
+#pragma unroll
+      for (int k2 = 0; k2 < 18; ++k2) Dm[k2] = __ffma2_rn(k2v, make_float2(gv[10 + 2 * k2], gv[11 + 2 * k2]), Dm[k2]);
+    }
+    const float2 pdt = make_float2(pg[g] * inv_dt, pg[g] * inv_dt);
+#pragma unroll
+    for (int a = 0; a < NEN / 2; ++a) bv2[a] = __ffma2_rn(make_float2(P[2 * a], P[2 * a + 1]), pdt, bv2[a]);
+  }
+}
+
 template <bool FULL>
 __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
   extern __shared__ __align__(16) float sm_ro[];
@@ -376,78 +458,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
           interp8(pn, pg);
           if (item + THREADS < items)  // prefetch the next item's fields while this one computes
             load_fields(r, S, (item + THREADS) / n_eq, (item + THREADS) % n_eq, kn, sn, pn);
-#pragma unroll
-          for (int g = 0; g < NG; ++g) {
-            const float4* G4 = reinterpret_cast<const float4*>(Ge + g * GEO);
-            float gv[GEO];
-#pragma unroll
-            for (int k2 = 0; k2 < GEO / 4 - 1; ++k2) {
-              const float4 x = G4[k2];
-              gv[4 * k2] = x.x;
-              gv[4 * k2 + 1] = x.y;
-              gv[4 * k2 + 2] = x.z;
-              gv[4 * k2 + 3] = x.w;
-            }
-            {
-              const float4 x = G4[GEO / 4 - 1];
-              gv[GEO - 4] = x.x;
-              gv[GEO - 3] = x.y;
-            }
-            const float dv = gv[0];
-            const float den = fmaf(ck, kg[g], gv[1] + sg[g]);
-            const float tau = den > 0.f ? __fdividef(1.f, den) : 0.f;
-            const float dvt = t_supg ? dv * tau : 0.f;
-            const float sigs = inv_dt + sg[g];
-            float P[NEN], Q[NEN];
-            if (FULL) {
-              // all terms: dV (N_a + tau u.gradN_a)((1/dt + s) N_b + u.gradN_b), one rank-1 product
-#pragma unroll
-              for (int a = 0; a < NEN; ++a) {
-                P[a] = fmaf(dvt, gv[2 + a], dv * hex_n(a, g));
-                Q[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
-              }
-#pragma unroll
-              for (int a = 0; a < NEN; ++a) {
-                const float2 pa = make_float2(P[a], P[a]);
-#pragma unroll
-                for (int b = 0; b < NEN / 2; ++b) Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
-              }
-            } else {
-              // dV N_a (sig N_b + [conv] u.gradN_b) + [supg] dV tau u.gradN_a ((1/dt + s) N_b + u.gradN_b)
-              const float sig = (t_mass ? inv_dt : 0.f) + (t_reac ? sg[g] : 0.f);
-              float Ps[NEN], R[NEN];
-#pragma unroll
-              for (int a = 0; a < NEN; ++a) {
-                P[a] = dv * hex_n(a, g);
-                Ps[a] = dvt * gv[2 + a];
-                Q[a] = sig * hex_n(a, g) + (t_conv ? gv[2 + a] : 0.f);
-                R[a] = fmaf(sigs, hex_n(a, g), gv[2 + a]);
-              }
-#pragma unroll
-              for (int a = 0; a < NEN; ++a) {
-                const float2 pa = make_float2(P[a], P[a]), ps = make_float2(Ps[a], Ps[a]);
-#pragma unroll
-                for (int b = 0; b < NEN / 2; ++b) {
-                  Am[a][b] = __ffma2_rn(pa, make_float2(Q[2 * b], Q[2 * b + 1]), Am[a][b]);
-                  Am[a][b] = __ffma2_rn(ps, make_float2(R[2 * b], R[2 * b + 1]), Am[a][b]);
-                }
-              }
-              if (!t_mass) {
-#pragma unroll
-                for (int a = 0; a < NEN; ++a) P[a] = 0.f;
-              }
-#pragma unroll
-              for (int a = 0; a < NEN; ++a) P[a] += Ps[a];
-            }
-            if (t_diff) {
-              const float2 k2v = make_float2(kg[g], kg[g]);
-#pragma unroll
-              for (int k2 = 0; k2 < 18; ++k2) Dm[k2] = __ffma2_rn(k2v, make_float2(gv[10 + 2 * k2], gv[11 + 2 * k2]), Dm[k2]);
-            }
-            const float2 pdt = make_float2(pg[g] * inv_dt, pg[g] * inv_dt);
-#pragma unroll
-            for (int a = 0; a < NEN / 2; ++a) bv2[a] = __ffma2_rn(make_float2(P[2 * a], P[2 * a + 1]), pdt, bv2[a]);
-          }
+          item_sums<FULL>(Ge, ck, kg, sg, pg, inv_dt, t_mass, t_conv, t_diff, t_reac, t_supg, Am, Dm, bv2);
         }  // has
         // add into the shared-memory rows (offsets are in row-window entries of neqs floats):
         // local rows a and a + 4 in round a & 3.  The plan lets two elements of a batch share
@@ -494,5 +505,108 @@ __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
     __syncthreads();
     flush_rows(r, win, t1 - 1, warp, THREADS / 32);
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ element-parallel Hex8
+
+// One CTA takes batches of `be` consecutive elements: node data into shared memory, the
+// geometry of the batch (one thread per (element, Gauss point)), then one thread per
+// (element, equation) item forms the same sums as the row-owned kernel and sends them out
+// by MODE: atomic adds into the CSR values and RHS, stores to the gather scratch, or the
+// matrix-free residual b^e - A^e phi^e added into r.  No schedule, no halo recompute.
+enum { EMODE_ATOMIC = 0, EMODE_SCRATCH = 1, EMODE_RESIDUAL = 2 };
+
+template <bool FULL, int MODE>
+__global__ void __launch_bounds__(THREADS, 1) k_hex8_elem(RoArgs r) {
+  extern __shared__ __align__(16) float sm_el[];
+  const AsmArgs<float>& A_ = r.a;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int be = r.be, n_eq = A_.eq_count;
+  float* geo = sm_el;
+  Stage S;
+  S.raw = geo + be * GEO_ELEM;
+  S.nid = reinterpret_cast<int32_t*>(S.raw + be * NEN * RAW);
+  S.off = nullptr;
+  const float inv_dt = (float)(1.0 / A_.dt);
+  const bool t_mass = A_.terms & FEA_TERM_MASS, t_conv = A_.terms & FEA_TERM_CONV,
+             t_diff = A_.terms & FEA_TERM_DIFF, t_reac = A_.terms & FEA_TERM_REAC,
+             t_supg = A_.terms & FEA_TERM_SUPG;
+  const int64_t N = A_.n_node, E = A_.n_elem;
+  const int64_t nb = (E + be - 1) / be;
+  for (int64_t bt = blockIdx.x; bt < nb; bt += gridDim.x) {
+    const int64_t e0 = bt * be;
+    const int nv = (int)((E - e0) < (int64_t)be ? (E - e0) : (int64_t)be);
+    __syncthreads();  // the previous batch is done with geo and the staged nodes
+    for (int i = tid; i < nv * NEN; i += THREADS) S.nid[i] = A_.conn[e0 * NEN + i];
+    __syncthreads();
+    for (int i = tid; i < nv * NEN * RAW; i += THREADS) {
+      const int node = i / RAW, c = i - node * RAW;
+      const int64_t n = S.nid[node];
+      S.raw[i] = c < 3 ? A_.xhi[(int64_t)c * N + n] : c < 6 ? A_.xlo[(int64_t)(c - 3) * N + n]
+                                                            : r.fnode[n * r.rec + 3 * n_eq + (c - 6)];
+    }
+    __syncthreads();
+    const int gw = (nv * NG + 31) / 32;
+    if (warp < gw) geometry(r, S, geo, tid >> 3, tid & 7, (tid >> 3) < nv);
+    __syncthreads();
+    const int items = nv * n_eq;
+    for (int item = tid; item < items; item += THREADS) {
+      const int el = item / n_eq, q = item - el * n_eq;
+      float kn[NEN], sn[NEN], pn[NEN];
+      load_fields(r, S, el, q, kn, sn, pn);
+      const float* Ge = geo + el * GEO_ELEM;
+      float kg[NG], sg[NG], pg[NG];
+      interp8(kn, kg);
+      interp8(sn, sg);
+      interp8(pn, pg);
+      float2 Am[NEN][NEN / 2], Dm[18], bv2[NEN / 2];
+#pragma unroll
+      for (int a = 0; a < NEN; ++a)
+#pragma unroll
+        for (int b = 0; b < NEN / 2; ++b) Am[a][b] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k2 = 0; k2 < 18; ++k2) Dm[k2] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int a = 0; a < NEN / 2; ++a) bv2[a] = make_float2(0.f, 0.f);
+      item_sums<FULL>(Ge, Ge[NG * GEO], kg, sg, pg, inv_dt, t_mass, t_conv, t_diff, t_reac, t_supg, Am, Dm, bv2);
+      const int64_t e = e0 + el;
+      const int32_t* ids = S.nid + el * NEN;
+      const int qg = A_.eq0 + q;
+      float phe[NEN];
+      if (MODE == EMODE_RESIDUAL) {
+#pragma unroll
+        for (int b = 0; b < NEN; ++b) phe[b] = __ldg(A_.phi_eval + (int64_t)qg * N + ids[b]);
+      }
+#pragma unroll
+      for (int a = 0; a < NEN; ++a) {
+        float row[NEN];
+#pragma unroll
+        for (int b = 0; b < NEN; b += 2) {
+          const int i0 = a <= b ? sym_index(a, b) : sym_index(b, a);
+          const int i1 = a <= b + 1 ? sym_index(a, b + 1) : sym_index(b + 1, a);
+          row[b] = Am[a][b / 2].x + ((i0 & 1) ? Dm[i0 >> 1].y : Dm[i0 >> 1].x);
+          row[b + 1] = Am[a][b / 2].y + ((i1 & 1) ? Dm[i1 >> 1].y : Dm[i1 >> 1].x);
+        }
+        const float ba = (a & 1) ? bv2[a / 2].y : bv2[a / 2].x;
+        if (MODE == EMODE_RESIDUAL) {
+          float y = ba;
+#pragma unroll
+          for (int b = 0; b < NEN; ++b) y = fmaf(-row[b], phe[b], y);
+          atomicAdd(A_.resid + (int64_t)qg * N + ids[a], y);
+        } else if (MODE == EMODE_SCRATCH) {
+          float* d = A_.em + ((e * (NEN * NEN + NEN)) + a * NEN) * n_eq + q;
+#pragma unroll
+          for (int b = 0; b < NEN; ++b) d[b * n_eq] = row[b];
+          A_.em[((e * (NEN * NEN + NEN)) + NEN * NEN + a) * n_eq + q] = ba;
+        } else {
+          const int32_t* pe = A_.pos + (e * NEN + a) * NEN;
+          float* vq = A_.values + (int64_t)qg * A_.nnz;
+#pragma unroll
+          for (int b = 0; b < NEN; ++b) atomicAdd(vq + __ldg(pe + b), row[b]);
+          atomicAdd(A_.rhs + (int64_t)qg * N + ids[a], ba);
+        }
+      }
+    }
   }
 }
