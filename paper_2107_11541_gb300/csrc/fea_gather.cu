@@ -8,10 +8,12 @@
 //
 // One CTA owns R consecutive rows, i.e. the contiguous CSR range [rowptr[r0], rowptr[r1])
 // of every equation, held in shared memory as acc[q][k - rowptr[r0]] and racc[q][r - r0].
-// One warp sums one row: for each incident element in ascending element order (the
-// order is fixed, so the result is bitwise reproducible), its lanes read the element
-// row, NEN columns x n_eq equations contiguous in the scratch, and add it in.  Distinct
-// rows own distinct positions, so no two warps touch the same word.  The CTA then writes
+// One warp sums one row over its incident elements in ascending element order (the order
+// is fixed, so the result is bitwise reproducible): the lanes first load the element rows
+// of several incident elements (NEN columns x n_eq equations plus the RHS, contiguous in
+// the scratch; the local index of the row's node comes from the pattern), then add them in
+// one element at a time.  Distinct rows own distinct positions, so no two warps touch the
+// same word.  The CTA then writes
 // each equation's range of values and RHS entries with consecutive threads on
 // consecutive addresses, once.
 #include <algorithm>
@@ -27,7 +29,6 @@ constexpr size_t GATHER_SMEM_MAX = 227 * 1024;
 
 struct GatherArgs {
   const float* em;
-  const int32_t* conn;
   const int32_t* pos;
   const int64_t* rowptr;
   const int64_t* inc_ptr;
@@ -165,7 +166,6 @@ size_t gather_scratch_bytes(int64_t n_elem, int nen, int n_eq) {
 fea_status launch_gather_f32(const AsmArgs<float>& a, fea_elem_t type, int maxcol, bool accumulate, cudaStream_t s) {
   GatherArgs g;
   g.em = a.em;
-  g.conn = a.conn;
   g.pos = a.pos;
   g.rowptr = a.rowptr;
   g.inc_ptr = a.inc_ptr;

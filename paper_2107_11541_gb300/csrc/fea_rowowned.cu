@@ -7,7 +7,8 @@
 // with plain stores, as soon as its last incident element has been processed:
 // no output zeroing, no global atomics, and the result does not depend on
 // scheduling (bitwise reproducible).  Elements on the boundary of a pencil are
-// computed by each unit that owns one of their nodes (halo recompute).
+// computed by each unit that owns one of their nodes (halo recompute).  Also here: the
+// element-parallel Hex8 kernel (no schedule) behind the atomic, gather and residual paths.
 //
 // Per element and Gauss point the geometry (Jacobian, det, inverse-transpose,
 // physical gradients, w det J, u.grad N_a, the symmetric products
@@ -32,11 +33,11 @@ namespace fea {
 namespace ro {
 
 constexpr int NEN = 8, NG = 8;
-constexpr int BEMAX = 32;               // elements per batch at most: geometry uses <= 6 warps, >= 2 flush
+constexpr int BEMAX = 32;               // elements per batch at most: one thread per (element, Gauss point)
 constexpr int THREADS = 256;            // 8 warps
 constexpr int ROUNDS = 4;               // scatter rounds: local rows a and a + 4 in round a & 3
 constexpr int round_of(int a) { return a & 3; }
-constexpr int LOOKAHEAD = 64;           // sweep positions scanned when colouring a batch
+constexpr int LOOKAHEAD = 64;           // sweep positions scanned when forming a batch
 constexpr int GEO = 48;                 // floats per Gauss point: dv, cu, ua[8], Gd[36], pad[2]
 constexpr int GEO_ELEM = NG * GEO + 4;  // + ck (4/h^2) and padding
 constexpr int OFFS = NEN * NEN + NEN;   // entry offsets per element visit (matrix, then RHS)
