@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
 enum { EMODE_ATOMIC = 0, EMODE_SCRATCH = 1, EMODE_RESIDUAL = 2 };
 
 template <bool FULL, int MODE>
-__global__ void __launch_bounds__(THREADS, 1) k_hex8_elem(RoArgs r) {
+__global__ void __launch_bounds__(THREADS, (MODE == EMODE_RESIDUAL && FULL) ? 2 : 1) k_hex8_elem(RoArgs r) {
   extern __shared__ __align__(16) float sm_el[];
   const AsmArgs<float>& A_ = r.a;
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -555,6 +555,60 @@ __global__ void __launch_bounds__(THREADS, 1) k_hex8_elem(RoArgs r) {
       const int el = item / n_eq, q = item - el * n_eq;
       float kn[NEN], sn[NEN], pn[NEN];
       load_fields(r, S, el, q, kn, sn, pn);
+      if (MODE == EMODE_RESIDUAL && FULL) {
+        // Matrix-free, without the element matrix: per Gauss point
+        //   y_a += P_a (phi_old_g / dt - (1/dt + s_g) phi_g - u.grad phi_g) - k_g sum_b D_ab phi_b
+        // with P_a = dV (N_a + tau u.grad N_a) (the full operator, whose trial part is
+        // (1/dt + s) N_b + u.grad N_b).
+        const float* Ge = geo + el * GEO_ELEM;
+        const float ck = Ge[NG * GEO];
+        const int32_t* ids = S.nid + el * NEN;
+        const int qg = A_.eq0 + q;
+        float ph[NEN], kg[NG], sg[NG], pg[NG], fg[NG];
+#pragma unroll
+        for (int b = 0; b < NEN; ++b) ph[b] = __ldg(A_.phi_eval + (int64_t)qg * N + ids[b]);
+        interp8(kn, kg);
+        interp8(sn, sg);
+        interp8(pn, pg);
+        interp8(ph, fg);
+        float y[NEN];
+#pragma unroll
+        for (int a = 0; a < NEN; ++a) y[a] = 0.f;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) {
+          const float* G = Ge + g * GEO;
+          const float dv = G[0];
+          const float den = fmaf(ck, kg[g], G[1] + sg[g]);
+          const float tau = den > 0.f ? __fdividef(1.f, den) : 0.f;
+          float ua[NEN], ugp = 0.f;
+#pragma unroll
+          for (int a = 0; a < NEN; a += 2) {  // u.grad N_a sits at offset 2 of the record: 8-byte aligned pairs
+            const float2 x = *reinterpret_cast<const float2*>(G + 2 + a);
+            ua[a] = x.x;
+            ua[a + 1] = x.y;
+          }
+#pragma unroll
+          for (int b = 0; b < NEN; ++b) ugp = fmaf(ua[b], ph[b], ugp);  // u.grad phi at g
+          const float rg = fmaf(-(inv_dt + sg[g]), fg[g], fmaf(pg[g], inv_dt, -ugp));
+          const float dvr = dv * rg, dvtr = dv * tau * rg;
+#pragma unroll
+          for (int a = 0; a < NEN; ++a) y[a] = fmaf(dvtr, ua[a], fmaf(dvr, hex_n(a, g), y[a]));
+          // diffusion: y -= k_g D phi, D symmetric (entries a <= b)
+          const float kgg = kg[g];
+#pragma unroll
+          for (int a = 0; a < NEN; ++a) {
+#pragma unroll
+            for (int b = a; b < NEN; ++b) {
+              const float d = kgg * G[10 + sym_index(a, b)];
+              y[a] = fmaf(-d, ph[b], y[a]);
+              if (b != a) y[b] = fmaf(-d, ph[a], y[b]);
+            }
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < NEN; ++a) atomicAdd(A_.resid + (int64_t)qg * N + ids[a], y[a]);
+        continue;
+      }
       const float* Ge = geo + el * GEO_ELEM;
       float kg[NG], sg[NG], pg[NG];
       interp8(kn, kg);
