@@ -73,3 +73,23 @@ def test_autotune_not_run_when_accumulating():
         assert np.array_equal(r2.cpu().numpy(), 2 * r1.cpu().numpy())
     finally:
         run.close()
+
+
+def test_tuning_several_equation_counts_keeps_each_choice():
+    """Tuning one equation count must not discard the schedules another count uses: after
+    tuning 4 and 1 equations, a 4-equation call launches only its chosen kernels again."""
+    w4 = G.make_workload(2, n=6, n_eq=4)
+    w1 = G.make_workload(2, n=6, n_eq=1)
+    run = GpuRun(w4.mesh)
+    try:
+        run.assemble(w4.fields, fea.FEA_F32_FUSED)
+        run.assemble(w1.fields, fea.FEA_F32_FUSED)
+        s4, g4 = fea.fea_tuned_strategy(run.pattern, 4)
+        l0 = fea.fea_kernel_launches()
+        v, r = run.assemble(w4.fields, fea.FEA_F32_FUSED)
+        assert fea.fea_kernel_launches() - l0 <= 2 * g4
+        assert fea.fea_tuned_strategy(run.pattern, 4) == (s4, g4)
+        ea, eb = compare_full(run, w4.fields, fea.FEA_F32_FUSED, values=v, rhs=r)
+        assert ea <= TOL_F32 and eb <= TOL_F32
+    finally:
+        run.close()
