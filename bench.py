@@ -207,6 +207,17 @@ def field_update_parity(mesh, phi0, phi_gpu, prm, seq):
     return {"nodes": int(idx.size), "updates": len(seq), "max_abs_err": err, "tol": 1e-5, "pass": err <= 1e-5}
 
 
+def aggregate_over_ranks(ms, kernel_ms, units_per_rank, world, dist, device):
+    """Replica runs: the slowest rank's step time (max over ranks) and the whole job's rate,
+    every rank's units divided by that time.  dist is torch.distributed or None (one rank)."""
+    if dist is not None:
+        import torch
+        t = torch.tensor([ms, kernel_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, kernel_ms = float(t[0]), float(t[1])
+    return ms, kernel_ms, units_per_rank * world / (ms * 1e-3)
+
+
 def config_dict(workload, w, nnz):
     m = w.mesh
     return {"workload": workload, "elem_type": G.NAMES[m.elem_type], "elements": m.n_elem, "nodes": m.n_node,
@@ -323,12 +334,7 @@ def main():
         fea.fea_graph_destroy(graph)
     ms = t0e.elapsed_time(t1e) / args.steps
     kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
-    if dist is not None:
-        t = torch.tensor([ms, kernel_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, kernel_ms = float(t[0]), float(t[1])
-    units = m.n_elem * q * world
-    value = units / (ms * 1e-3)
+    ms, kernel_ms, value = aggregate_over_ranks(ms, kernel_ms, m.n_elem * q, world, dist, "cuda")
 
     # roofline of the dominant kernel
     peaks = measured_peaks()
