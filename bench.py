@@ -241,6 +241,8 @@ def main():
     ap.add_argument("--cells", type=int, default=None, help="shrink to this many cells per axis (profiling)")
     ap.add_argument("--residual", action="store_true",
                     help="also time the matrix-free residual r = b - A phi (fea_residual) on the same workload")
+    ap.add_argument("--spmv", action="store_true",
+                    help="also time the batched SpMV y_q = A_q x_q (fea_spmv) on the assembled matrices")
     ap.add_argument("--graph", type=int, default=None,
                     help="1: time the K steps as one CUDA graph of K (assemble, field update) time steps "
                          "(default on for hex8_256_32eq)")
@@ -382,6 +384,21 @@ def main():
 
     if rank == 0 and not args.no_parity:
         out["parity"] = sampled_parity(w, values, rhs, p, nnz)
+    if args.spmv:
+        xs = torch.ones((q, m.n_node), dtype=torch.float32, device="cuda")
+        ys = torch.empty_like(xs)
+        fea.fea_spmv(p, values, xs, ys, q, 0, stream)
+        sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sa.record(stream)
+        for _ in range(5):
+            fea.fea_spmv(p, values, xs, ys, q, 0, stream)
+        sb.record(stream)
+        torch.cuda.synchronize()
+        sms = sa.elapsed_time(sb) / 5
+        sbytes = 4 * q * nnz + 4 * nnz + 8 * (m.n_node + 1) + 2 * 4 * q * m.n_node  # values, colind, rowptr, x, y
+        out["spmv"] = {"ms": sms, "algorithmic_bytes": sbytes, "achieved_gbs": sbytes / (sms * 1e-3) / 1e9,
+                       "frac_of_hbm": sbytes / (sms * 1e-3) / 1e9 / hbm_peak}
+        del xs, ys
     if args.residual:
         r = torch.empty((q, m.n_node), dtype=torch.float32, device="cuda")
         ro = fea.fea_default_opts()

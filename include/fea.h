@@ -257,6 +257,16 @@ FEA_API fea_status fea_graph_launch(fea_graph* graph);
 FEA_API fea_status fea_graph_destroy(fea_graph* graph);
 
 /*
+ * fea_spmv -- y_q = A_q x_q for the n_eq FP32 matrices assembled on this pattern (the
+ * operator the solver of Sec. 2 applies in its PCG).  The pattern's column indices are read
+ * once per row for all equations.
+ *   values [n_eq][nnz], x and y [n_eq][n_node] float DEVICE pointers; accumulate != 0 adds
+ *   into y.  Enqueued on `stream` (cudaStream_t, NULL = legacy default stream).
+ */
+FEA_API fea_status fea_spmv(const fea_pattern* pattern, const float* values, const float* x, float* y, int32_t n_eq,
+                            int32_t accumulate, void* stream);
+
+/*
  * fea_tuned_strategy -- the scatter (fea_scatter) and equation-group count that
  * FEA_SCATTER_AUTO settled on for this pattern and n_eq.  FEA_ERR_STATE if no FP32
  * FEA_SCATTER_AUTO call has tuned that equation count yet.  Host only; does not wait.

@@ -28,7 +28,7 @@ EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_destroy", "fea_mesh_
            "fea_pattern_build", "fea_pattern_get", "fea_pattern_destroy", "fea_assemble", "fea_residual",
            "fea_assemble_host",
            "fea_pack_plan", "fea_csr_rowptr_noalloc", "fea_update_fields", "fea_graph_capture_steps",
-           "fea_graph_launch", "fea_graph_destroy", "fea_tuned_strategy", "fea_cancel_rows", "fea_last_error",
+           "fea_graph_launch", "fea_graph_destroy", "fea_spmv", "fea_tuned_strategy", "fea_cancel_rows", "fea_last_error",
            "fea_kernel_launches", "fea_version"]
 
 
@@ -75,6 +75,7 @@ def lib(path: str = LIB_PATH):
                                               vp, i32, C.POINTER(vp)]
         L.fea_graph_launch.argtypes = [vp]
         L.fea_tuned_strategy.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
+        L.fea_spmv.argtypes = [vp, vp, vp, vp, i32, i32, vp]
         L.fea_cancel_rows.argtypes = [vp, i32, C.POINTER(i64)]
         L.fea_graph_destroy.argtypes = [vp]
         L.fea_last_error.restype = C.c_char_p
@@ -217,6 +218,11 @@ def fea_graph_launch(graph):
 
 def fea_graph_destroy(graph):
     _check(lib().fea_graph_destroy(graph))
+
+
+def fea_spmv(pattern, values, x, y, n_eq: int, accumulate: int = 0, stream=None):
+    """y[q] = A_q x[q] for all equations (float32 CUDA tensors [n_eq][nnz], [n_eq][N])."""
+    _check(lib().fea_spmv(pattern, _ptr(values), _ptr(x), _ptr(y), int(n_eq), int(accumulate), _stream_ptr(stream)))
 
 
 def fea_tuned_strategy(pattern, n_eq: int):
