@@ -248,6 +248,19 @@ struct AsmArgs {
   uint32_t* status;
 };
 
+// Asynchronous global -> shared copies (4 bytes, or 16 bytes with both addresses 16-byte
+// aligned); a thread's copies become visible to the CTA after cp_async_wait_all and a barrier.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Launchers (defined in the kernel translation units).
 fea_status launch_generic_f64(const AsmArgs<double>& a, fea_elem_t type, cudaStream_t s);
 fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s);
