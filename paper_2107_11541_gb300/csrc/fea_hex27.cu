@@ -2,26 +2,27 @@
 // equations): the 27 x 27 matrices of all equations of an element share its geometry.
 //
 // Per Gauss point g (Sec. 4.2, Listing 1 extended to the full Galerkin + SUPG operator):
-//   A_ab = sum_g P_a(g) Q_b(g) + sum_g k_g D_ab(g),  b_a = sum_g P_a(g) phi_g / dt,
+//   A_ab = sum_g P_a(g) Q_b(g) + sum_g dV k_g D_ab(g),  b_a = sum_g P_a(g) phi_g / dt,
 //   P_a = dV (N_a + tau u.grad N_a),  Q_b = (1/dt + s) N_b + u.grad N_b,
-//   D_ab = dV grad N_a . grad N_b   (symmetric, the same for every equation).
+//   D_ab = grad N_a . grad N_b   (symmetric, the same for every equation).
+// The RHS rides along as column 27 of Q (Q_27(g) = phi_g / dt), so b_a = (P^T Q)_a,27.
 // Steps, each spread over the CTA's threads with a barrier between:
 //   0. the element's node data (coordinates as FP32 hi/lo, velocity, k, s, phi_old, and the
 //      CSR positions for the atomic scatter) arrive in a staging buffer by cp.async, issued
-//      during the previous element's contraction (connectivity one more phase ahead);
+//      after the previous element's contraction (connectivity earlier, with its first step);
 //   1. x_a - x_0, u_g;  2. J per (g, i, j);  3. det J and J^-T per g (FP64 when badly
 //      conditioned), dV;  4. grad N and u.grad N per (g, a), h = V^(1/3)/2;
-//   5. k, s, phi, tau, 1/dt + s per (equation, g), the diffusion weights dV k_g; D per
-//      (a <= b, g) without dV, one thread per symmetric entry;
+//   5. k, s, phi, tau, 1/dt + s per (equation, g) and the diffusion weights dV k_g; D in
+//      4 x 4 blocks (a-block <= b-block), one thread per (g, block pair);
 //   6. P and Q per (equation, g, four columns);
-//   7. the contractions in registers: P^T Q as 8 x 8 tiles over the 27 points, the
-//      diffusion as 8 symmetric entries x all equations (the D loads are shared by the
-//      equations), 16-byte shared loads feeding packed FP32x2 FMAs; the RHS on the threads
-//      left over;
-//   8. P^T Q tiles and the symmetric diffusion sums to shared memory (separate arrays);
-//   9. out: A = P^T Q + diffusion (entry (a, b) of the symmetric part looked up in a table),
-//      to the gather scratch em[e][entry][q], as atomic adds into the CSR values and RHS
-//      (one position load per entry for all equations), or as the matrix-free residual.
+//   7. the contractions in registers, all as one kind of task: a 16 x 4 outer product summed
+//      over the 27 points, fed by 16-byte shared loads into packed FP32x2 FMAs.  A P^T Q task
+//      covers 16 rows a x 4 columns b of one equation (2 x 7 tasks per equation); a
+//      diffusion task covers 16 entries of D (one 4 x 4 block) x 4 equations;
+//   8. the results to shared memory with 16-byte stores;
+//   9. out: A = P^T Q + diffusion (the D entry of (a, b) from a table), to the gather
+//      scratch em[e][entry][q], as atomic adds into the CSR values and RHS (one position
+//      load per entry for all equations), or as the matrix-free residual.
 #include <algorithm>
 
 #include "fea_internal.cuh"
@@ -29,17 +30,24 @@
 namespace fea {
 namespace {
 
-constexpr int NN = 27, PAD = 28;       // nodes / Gauss points; padded row length
-constexpr int SYM = NN * (NN + 1) / 2;  // 378 symmetric entries
-constexpr int DSTRIDE = 384;            // D row per Gauss point (multiple of 8)
-constexpr int ENT = NN * NN + NN;       // element matrix entries and RHS entries
+constexpr int NN = 27, PAD = 28;          // nodes / Gauss points; padded row length
+constexpr int NB = 7;                     // 4-wide blocks of a padded row
+constexpr int NBP = NB * (NB + 1) / 2;    // 28 blocks (A <= B) of the symmetric D
+constexpr int BPS = 20;                   // a block pair's 16 entries, padded: 8 consecutive pairs on distinct banks
+constexpr int DSTRIDE = NBP * BPS;        // D per Gauss point
+constexpr int DQS = 564;                  // one equation's diffusion sums: >= NBP * BPS, 20 mod 32
+constexpr int ENT = NN * NN + NN;         // element matrix entries and RHS entries
+constexpr int RQ = NN * PAD;              // one equation's results: rows a, columns b and the RHS (27)
 constexpr int H27_THREADS = 256;
+constexpr int H27_QMAX = 12;
+static_assert(H27_QMAX * 2 * NB + NBP * (H27_QMAX / 4) <= H27_THREADS, "one task per thread");
+static_assert(NBP * BPS <= DQS && DQS % 4 == 0 && H27_QMAX * DQS <= NN * DSTRIDE, "diffusion sums fit where D was");
 
 // Shared-memory layout in floats; QP = equations padded to a multiple of 4; SR staged rows
-// of 27 node values: x hi (3), x lo (3), u (3), then k, s, phi_old of each equation.
+// of 27 node values (padded to 28): x hi (3), x lo (3), u (3), then k, s, phi_old per equation.
 struct H27Layout {
-  int QP, SR, nt, dnt, rowp, wq, sym, cn, stage, spos, xd, jg, dv, un, ug, gr, ua, kgt, sg, pg, tau, sig, p, q, d,
-      ab, rhs, misc, total;
+  int QP, SR, nt, dnt, rowp, wq, sym, bpt, cn, stage, spos, xd, jg, dv, un, ug, gr, ua, kgt, pg, tau, sig, p, q, d,
+      misc, total;
   __host__ __device__ H27Layout(int Q) {
     QP = (Q + 3) & ~3;
     SR = 9 + 3 * Q;
@@ -49,41 +57,48 @@ struct H27Layout {
     o = (o + 1) & ~1;
     rowp = o;  o += 2 * SR;            // source array of staged row r (64-bit pointers)
     wq = o;    o += NN;                // Gauss weights
-    sym = o;   o += (NN * NN + 1) / 2; // symmetric index of entry (a, b) (16-bit)
+    sym = o;   o += (NN * NN + 1) / 2; // diffusion slot of (a, b) (16-bit)
+    bpt = o;   o += NBP;               // (A, B) of block pair bp, packed A | B << 8 (int bits)
     cn = o;    o += 2 * PAD;           // connectivity, two buffers (int bits)
-    stage = o; o += 2 * SR * NN;       // staged node data, two buffers [buf][row][a]
+    o = (o + 3) & ~3;
+    stage = o; o += 2 * SR * PAD;      // staged node data, two buffers [buf][row][a]
     spos = o;  o += 2 * NN * NN;       // staged CSR positions, two buffers (int bits)
     xd = o;    o += NN * 3;            // x_a - x_0          [a][i]
     jg = o;    o += NN * 9;            // J, then J^-T       [g][3][3]
     dv = o;    o += NN;                // w det J            [g]
     un = o;    o += NN;                // |u_g|
     ug = o;    o += NN * 3;            // u_g                [g][i]
-    o = (o + 3) & ~3;                  // 16-byte rows for the float4 loads below
+    o = (o + 3) & ~3;                  // 16-byte rows for the float4 accesses below
     gr = o;    o += NN * 3 * PAD;      // grad N             [g][i][a]
     ua = o;    o += NN * PAD;          // u.grad N           [g][a]
     kgt = o;   o += NN * QP;           // dV k_g             [g][q]
-    sg = o;    o += Q * NN;            // s_g                [q][g]
-    pg = o;    o += Q * NN;            // phi_g
+    pg = o;    o += Q * NN;            // phi_g              [q][g]
     tau = o;   o += Q * NN;
     sig = o;   o += Q * NN;            // 1/dt + s_g
     o = (o + 3) & ~3;
-    p = o;     o += Q * NN * PAD;      // P [q][g][a]; after the contractions P^T Q and the RHS [q][entry]
-    q = o;     o += Q * NN * PAD;      // Q                  [q][g][b]
-    d = o;     o += NN * DSTRIDE;      // grad N_a . grad N_b [g][sym]; after the contractions [q][sym]
-    ab = o;    o += DSTRIDE;           // (a, b) of symmetric entry k, packed a | b << 8 (int bits)
-    rhs = o;   o += Q * NN;            // b_a                [q][a]
+    p = o;     o += Q * NN * PAD;      // P [q][g][a]; after the contractions P^T Q [q][a][b], b = 27: RHS
+    q = o;     o += Q * NN * PAD;      // Q [q][g][b]
+    d = o;     o += NN * DSTRIDE;      // D [g][pair][BPS]; after the contractions the diffusion sums [q][pair][BPS]
     misc = o;  o += 4;                 // h
     total = o;
   }
 };
 
-// Index of entry (a, b) in the row-major upper triangle (row a starts at a NN - a (a - 1) / 2).
-__device__ __forceinline__ int sym_index(int a, int b) {
-  const int lo = min(a, b), hi = max(a, b);
-  return lo * NN - lo * (lo - 1) / 2 + (hi - lo);
+// Block pair (A <= B) of the 7 x 7 block grid, row-major upper triangle.
+__host__ __device__ inline int block_pair(int A, int B) { return A * NB - A * (A - 1) / 2 + (B - A); }
+
+// Slot of grad N_a . grad N_b among one equation's diffusion sums: entry r * 4 + c of block
+// pair (A, B) is (4A + r, 4B + c), and pair bp starts at bp * BPS.
+__host__ __device__ inline int d_slot(int a, int b) {
+  if (a / 4 > b / 4) {
+    const int t = a;
+    a = b;
+    b = t;
+  }
+  return block_pair(a / 4, b / 4) * BPS + (a & 3) * 4 + (b & 3);
 }
 
-template <int QMAX, bool EM>
+template <bool EM>
 __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
   extern __shared__ __align__(16) float sm27[];
   const int Q = p.eq_count;
@@ -92,12 +107,10 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
   const int64_t N = p.n_node;
   const float inv_dt = (float)(1.0 / p.dt);
   const bool stage_pos = !EM && p.resid == nullptr;  // the atomic scatter reads pos[e]
-  constexpr int DB = 8;                          // symmetric entries per diffusion task
-  constexpr int ACC = DB * QMAX / 2 > 32 ? DB * QMAX / 2 : 32;
-  const int n_pq = Q * 16;                       // (q, a-block, b-block) tiles of 8 x 8
-  const int n_d = (SYM + DB - 1) / DB;           // n_pq + n_d <= 12 * 16 + 48 = 240 threads
-  int* abt = reinterpret_cast<int*>(sm27 + L.ab);
+  const int n_pq = Q * 2 * NB;                   // (q, 16-row block, 4-column block)
+  const int n_task = n_pq + NBP * (L.QP / 4);    // + (block pair, 4 equations)
   uint16_t* symt = reinterpret_cast<uint16_t*>(sm27 + L.sym);
+  int* bpt = reinterpret_cast<int*>(sm27 + L.bpt);
   const float** rowp = reinterpret_cast<const float**>(sm27 + L.rowp);
 
   // constant tables
@@ -116,9 +129,9 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
     }
     sm27[L.nt + i] = v;
   }
-  if (tid < NN)
-    for (int b = tid, k = tid * NN - tid * (tid - 1) / 2; b < NN; ++b, ++k) abt[k] = tid | (b << 8);
-  for (int i = tid; i < NN * NN; i += H27_THREADS) symt[i] = (uint16_t)sym_index(i / NN, i - (i / NN) * NN);
+  for (int i = tid; i < NN * NN; i += H27_THREADS) symt[i] = (uint16_t)d_slot(i / NN, i - (i / NN) * NN);
+  if (tid < NB)
+    for (int B = tid; B < NB; ++B) bpt[block_pair(tid, B)] = tid | (B << 8);
   for (int r = tid; r < L.SR; r += H27_THREADS) {
     const float* src;
     if (r < 3) src = p.xhi + (int64_t)r * N;
@@ -130,6 +143,7 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
     }
     rowp[r] = src;
   }
+  for (int r = tid; r < 2 * L.SR; r += H27_THREADS) sm27[L.stage + r * PAD + NN] = 0.f;  // padded column
   // the first element's connectivity (plain loads) and node data (cp.async)
   if (blockIdx.x < p.n_elem && tid < NN)
     reinterpret_cast<int*>(sm27 + L.cn)[tid] = p.conn[(int64_t)blockIdx.x * NN + tid];
@@ -137,10 +151,10 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
   // staged node data of element e into buffer buf (connectivity already in cn[buf])
   auto stage_issue = [&](int64_t e, int buf) {
     const int* cb = reinterpret_cast<const int*>(sm27 + L.cn + buf * PAD);
-    float* dst = sm27 + L.stage + buf * L.SR * NN;
+    float* dst = sm27 + L.stage + buf * L.SR * PAD;
     for (int i = tid; i < L.SR * NN; i += H27_THREADS) {
       const int r = i / NN, a = i - r * NN;
-      cp_async4(dst + i, rowp[r] + cb[a]);
+      cp_async4(dst + r * PAD + a, rowp[r] + cb[a]);
     }
     if (stage_pos) {
       const int32_t* pe = p.pos + e * (NN * NN);
@@ -155,7 +169,7 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
   for (int64_t e = blockIdx.x; e < p.n_elem; e += gridDim.x, cur ^= 1) {
     const int64_t en = e + gridDim.x;
     const int* ce = reinterpret_cast<const int*>(sm27 + L.cn + cur * PAD);
-    const float* st = sm27 + L.stage + cur * L.SR * NN;  // [row][a]
+    const float* st = sm27 + L.stage + cur * L.SR * PAD;  // [row][a]
     cp_async_wait_all();
     __syncthreads();  // element e's staged data is visible; the previous element's results are written
     if (en < p.n_elem && tid < NN) cp_async4(sm27 + L.cn + (cur ^ 1) * PAD + tid, p.conn + en * NN + tid);
@@ -163,10 +177,10 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
     // 1. x_a - x_0 (hi/lo split), u_g = sum_a N_a(g) u_a
     if (tid < NN * 3) {
       const int a = tid / 3, c = tid - a * 3;
-      sm27[L.xd + tid] = (st[c * NN + a] - st[c * NN]) + (st[(3 + c) * NN + a] - st[(3 + c) * NN]);
+      sm27[L.xd + tid] = (st[c * PAD + a] - st[c * PAD]) + (st[(3 + c) * PAD + a] - st[(3 + c) * PAD]);
     } else if (tid >= 128 && tid < 128 + NN * 3) {
       const int i = tid - 128, g = i / 3, c = i - g * 3;
-      const float* u = st + (6 + c) * NN;
+      const float* u = st + (6 + c) * PAD;
       float s = 0.f;
       for (int a = 0; a < NN; ++a) s = fmaf(sm27[L.nt + g * PAD + a], u[a], s);
       sm27[L.ug + i] = s;
@@ -245,24 +259,34 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
       sm27[L.misc] = cbrtf(v) * 0.5f;  // h = V^(1/3) / 2
     }
     __syncthreads();
-    // 5a. k, s, phi, tau, 1/dt + s per (q, g); the diffusion weight dV k_g
+    // 5a. k, s, phi, tau, 1/dt + s per (q, g) (padded node columns are zero); the weight dV k_g
     {
       const float h = sm27[L.misc], c_k = 4.0f / (h * h), c_u = 2.0f / h;
       for (int i = tid; i < Q * NN; i += H27_THREADS) {
         const int q = i / NN, g = i - q * NN;
-        const float* fk = st + (9 + q) * NN;
-        const float* fs = st + (9 + Q + q) * NN;
-        const float* fp = st + (9 + 2 * Q + q) * NN;
+        const float4* n4 = reinterpret_cast<const float4*>(sm27 + L.nt + g * PAD);
+        const float4* k4 = reinterpret_cast<const float4*>(st + (9 + q) * PAD);
+        const float4* s4 = reinterpret_cast<const float4*>(st + (9 + Q + q) * PAD);
+        const float4* p4 = reinterpret_cast<const float4*>(st + (9 + 2 * Q + q) * PAD);
         float kg = 0.f, sg = 0.f, pg = 0.f;
-        for (int a = 0; a < NN; ++a) {
-          const float na = sm27[L.nt + g * PAD + a];
-          kg = fmaf(na, fk[a], kg);
-          sg = fmaf(na, fs[a], sg);
-          pg = fmaf(na, fp[a], pg);
+#pragma unroll
+        for (int c = 0; c < NB; ++c) {
+          const float4 n = n4[c], k = k4[c], sv = s4[c], ph = p4[c];
+          kg = fmaf(n.x, k.x, kg);
+          kg = fmaf(n.y, k.y, kg);
+          kg = fmaf(n.z, k.z, kg);
+          kg = fmaf(n.w, k.w, kg);
+          sg = fmaf(n.x, sv.x, sg);
+          sg = fmaf(n.y, sv.y, sg);
+          sg = fmaf(n.z, sv.z, sg);
+          sg = fmaf(n.w, sv.w, sg);
+          pg = fmaf(n.x, ph.x, pg);
+          pg = fmaf(n.y, ph.y, pg);
+          pg = fmaf(n.z, ph.z, pg);
+          pg = fmaf(n.w, ph.w, pg);
         }
         const float den = c_k * kg + c_u * sm27[L.un + g] + sg;
         sm27[L.kgt + g * L.QP + q] = sm27[L.dv + g] * kg;
-        sm27[L.sg + i] = sg;
         sm27[L.pg + i] = pg;
         sm27[L.tau + i] = den > 0.f ? 1.0f / den : 0.f;
         sm27[L.sig + i] = inv_dt + sg;
@@ -272,28 +296,32 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
         sm27[L.kgt + g * L.QP + q] = 0.f;
       }
     }
-    // 5b. D_ab(g) = grad N_a . grad N_b, a <= b, one thread per symmetric entry (padding zero):
-    // entry tid, and entry tid + 128 on the upper half of the threads (the lower ones may have
-    // two (q, g) items above)
-    for (int rep = 0; rep < 2; ++rep) {
-      const int k = rep == 0 ? tid : tid + (DSTRIDE - H27_THREADS);
-      if (k >= DSTRIDE || (rep == 1 && tid < 2 * H27_THREADS - DSTRIDE)) break;
-      float* Dk = sm27 + L.d + k;
-      if (k < SYM) {
-        const int ab2 = abt[k], a = ab2 & 0xff, b = ab2 >> 8;
-#pragma unroll 9
-        for (int g = 0; g < NN; ++g) {
-          const float* gg = sm27 + L.gr + g * 3 * PAD;
-          Dk[g * DSTRIDE] = gg[a] * gg[b] + gg[PAD + a] * gg[PAD + b] + gg[2 * PAD + a] * gg[2 * PAD + b];
-        }
-      } else {
-        for (int g = 0; g < NN; ++g) Dk[g * DSTRIDE] = 0.f;
+    // 5b. D_ab(g) = grad N_a . grad N_b in 4 x 4 blocks (A <= B), one thread per (g, block pair)
+    for (int i = tid; i < NN * NBP; i += H27_THREADS) {
+      const int g = i / NBP, bp = i - g * NBP, AB = bpt[bp], A = AB & 0xff, B = AB >> 8;
+      const float* gg = sm27 + L.gr + g * 3 * PAD;
+      float4 xa[3], xb[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        xa[c] = *reinterpret_cast<const float4*>(gg + c * PAD + 4 * A);
+        xb[c] = *reinterpret_cast<const float4*>(gg + c * PAD + 4 * B);
+      }
+      float4* dst = reinterpret_cast<float4*>(sm27 + L.d + g * DSTRIDE + bp * BPS);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const float a0 = (&xa[0].x)[r], a1 = (&xa[1].x)[r], a2 = (&xa[2].x)[r];
+        float4 v;
+        v.x = a0 * xb[0].x + a1 * xb[1].x + a2 * xb[2].x;
+        v.y = a0 * xb[0].y + a1 * xb[1].y + a2 * xb[2].y;
+        v.z = a0 * xb[0].z + a1 * xb[1].z + a2 * xb[2].z;
+        v.w = a0 * xb[0].w + a1 * xb[1].w + a2 * xb[2].w;
+        dst[r] = v;
       }
     }
     __syncthreads();
-    // 6. P and Q per (q, g, four columns a); the padded column is zero because N and u.grad N are
-    for (int i = tid; i < Q * NN * (PAD / 4); i += H27_THREADS) {
-      const int qg = i / (PAD / 4), c4 = (i - qg * (PAD / 4)) * 4, g = qg - (qg / NN) * NN;
+    // 6. P and Q per (q, g, four columns a); the padded column: P 0, Q phi_g / dt (the RHS)
+    for (int i = tid; i < Q * NN * NB; i += H27_THREADS) {
+      const int qg = i / NB, c4 = (i - qg * NB) * 4, g = qg - (qg / NN) * NN;
       const float4 na = *reinterpret_cast<const float4*>(sm27 + L.nt + g * PAD + c4);
       const float4 ua = *reinterpret_cast<const float4*>(sm27 + L.ua + g * PAD + c4);
       const float dvg = sm27[L.dv + g], t = sm27[L.tau + qg], sgm = sm27[L.sig + qg];
@@ -305,102 +333,72 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
       qv.x = fmaf(sgm, na.x, ua.x);
       qv.y = fmaf(sgm, na.y, ua.y);
       qv.z = fmaf(sgm, na.z, ua.z);
-      qv.w = fmaf(sgm, na.w, ua.w);
+      qv.w = c4 == PAD - 4 ? sm27[L.pg + qg] * inv_dt : fmaf(sgm, na.w, ua.w);
       *reinterpret_cast<float4*>(sm27 + L.p + qg * PAD + c4) = pv;
       *reinterpret_cast<float4*>(sm27 + L.q + qg * PAD + c4) = qv;
     }
     cp_async_wait_all();  // the next element's connectivity
     __syncthreads();
-    // 7. the next element's node data starts to arrive; contractions in registers; RHS
-    if (en < p.n_elem) stage_issue(en, cur ^ 1);
-    float2 acc2[ACC];  // PQ task: 8 x 8 tile; diffusion task: DB entries x QMAX equations
-#pragma unroll
-    for (int i = 0; i < ACC; ++i) acc2[i] = make_float2(0.f, 0.f);
+    // 7. the contractions, acc[r][c] = sum_g x_r(g) y_c(g)
     const int task = tid;
-    int tq = 0, ab = 0, bb = 0;
-    if (task < n_pq) {
-      tq = task / 16;
-      ab = (task / 4) & 3;
-      bb = task & 3;
-      const float* P = sm27 + L.p + tq * NN * PAD + ab * 8;
-      const float* Qm = sm27 + L.q + tq * NN * PAD + bb * 8;
+    const float* X;  // 16 consecutive values per point, stride sx
+    const float* Y;  // 4 consecutive values per point, stride sy
+    int sx, sy;
+    if (task < n_pq) {  // P^T Q: rows 16 rb .. 16 rb + 15 (rows past 26 are discarded), columns 4 cb ..
+      const int tq = task / (2 * NB), rem = task - tq * 2 * NB, rb = rem / NB, cb = rem - rb * NB;
+      X = sm27 + L.p + tq * NN * PAD + rb * 16;
+      Y = sm27 + L.q + tq * NN * PAD + cb * 4;
+      sx = sy = PAD;
+    } else {  // diffusion: the 16 entries of block pair bp x equations 4 qb ..
+      const int t = min(task, n_task - 1) - n_pq, qb = t / NBP, bp = t - qb * NBP;
+      X = sm27 + L.d + bp * BPS;
+      Y = sm27 + L.kgt + qb * 4;
+      sx = DSTRIDE;
+      sy = L.QP;
+    }
+    float2 acc2[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc2[i] = make_float2(0.f, 0.f);
+    if (task < n_task) {
 #pragma unroll 3
       for (int g = 0; g < NN; ++g) {
-        const float4 p0 = *reinterpret_cast<const float4*>(P + g * PAD);
-        const float4 p1 = *reinterpret_cast<const float4*>(P + g * PAD + 4);
-        const float4 q0 = *reinterpret_cast<const float4*>(Qm + g * PAD);
-        const float4 q1 = *reinterpret_cast<const float4*>(Qm + g * PAD + 4);
-        const float pa[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
-        const float2 qb[4] = {make_float2(q0.x, q0.y), make_float2(q0.z, q0.w), make_float2(q1.x, q1.y),
-                              make_float2(q1.z, q1.w)};
+        const float4* xg = reinterpret_cast<const float4*>(X + g * sx);
+        const float4 x0 = xg[0], x1 = xg[1], x2 = xg[2], x3 = xg[3];
+        const float4 y = *reinterpret_cast<const float4*>(Y + g * sy);
+        const float xr[16] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w,
+                              x2.x, x2.y, x2.z, x2.w, x3.x, x3.y, x3.z, x3.w};
+        const float2 y01 = make_float2(y.x, y.y), y23 = make_float2(y.z, y.w);
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-          for (int b = 0; b < 4; ++b) acc2[a * 4 + b] = __ffma2_rn(make_float2(pa[a], pa[a]), qb[b], acc2[a * 4 + b]);
-      }
-    } else if (task >= n_pq + n_d) {
-      // threads without a contraction task: the RHS, b_a = sum_g P_a phi_g / dt
-      for (int i = task - (n_pq + n_d); i < Q * NN; i += H27_THREADS - (n_pq + n_d)) {
-        const int qq = i / NN, a = i - qq * NN;
-        float s0 = 0.f;
-        for (int g = 0; g < NN; ++g) s0 = fmaf(sm27[L.p + (qq * NN + g) * PAD + a], sm27[L.pg + qq * NN + g], s0);
-        sm27[L.rhs + i] = s0 * inv_dt;
-      }
-    } else {
-      const int k0 = (task - n_pq) * DB;
-      const float* D = sm27 + L.d + k0;
-      const float* K = sm27 + L.kgt;
-#pragma unroll 3
-      for (int g = 0; g < NN; ++g) {
-        float dv8[DB];
-#pragma unroll
-        for (int j = 0; j < DB; j += 4) {
-          const float4 x = *reinterpret_cast<const float4*>(D + g * DSTRIDE + j);
-          dv8[j] = x.x;
-          dv8[j + 1] = x.y;
-          dv8[j + 2] = x.z;
-          dv8[j + 3] = x.w;
+        for (int r = 0; r < 16; ++r) {
+          acc2[2 * r] = __ffma2_rn(make_float2(xr[r], xr[r]), y01, acc2[2 * r]);
+          acc2[2 * r + 1] = __ffma2_rn(make_float2(xr[r], xr[r]), y23, acc2[2 * r + 1]);
         }
-        float2 kq[QMAX / 2];
-#pragma unroll
-        for (int j = 0; j < QMAX; j += 4) {
-          const float4 x = *reinterpret_cast<const float4*>(K + g * L.QP + j);
-          kq[j / 2] = make_float2(x.x, x.y);
-          kq[j / 2 + 1] = make_float2(x.z, x.w);
-        }
-#pragma unroll
-        for (int j = 0; j < DB; ++j)
-#pragma unroll
-          for (int c = 0; c < QMAX / 2; ++c)
-            acc2[j * (QMAX / 2) + c] = __ffma2_rn(make_float2(dv8[j], dv8[j]), kq[c], acc2[j * (QMAX / 2) + c]);
       }
     }
     __syncthreads();  // P, Q and D are no longer read: P^T Q goes where P was, the diffusion sums where D was
-    float* R = sm27 + L.p;   // [q][ENT]: P^T Q, then the RHS
-    float* Dq = sm27 + L.d;  // [q][DSTRIDE]: sum_g dV k_g grad N_a . grad N_b, entry sym(a, b)
+    if (en < p.n_elem) stage_issue(en, cur ^ 1);  // the next element's node data starts to arrive
+    float* R = sm27 + L.p;   // [q][a][PAD]: P^T Q, column 27 the RHS
+    float* Dq = sm27 + L.d;  // [q][DQS]: sum_g dV k_g grad N_a . grad N_b at d_slot(a, b)
     if (task < n_pq) {
+      const int tq = task / (2 * NB), rem = task - tq * 2 * NB, rb = rem / NB, cb = rem - rb * NB;
 #pragma unroll
-      for (int a = 0; a < 8; ++a)
+      for (int r = 0; r < 16; ++r)
+        if (rb * 16 + r < NN)
+          *reinterpret_cast<float4*>(R + tq * RQ + (rb * 16 + r) * PAD + cb * 4) =
+              make_float4(acc2[2 * r].x, acc2[2 * r].y, acc2[2 * r + 1].x, acc2[2 * r + 1].y);
+    } else if (task < n_task) {
+      const int t = task - n_pq, qb = t / NBP, bp = t - qb * NBP;
+      float* d0 = Dq + qb * 4 * DQS + bp * BPS;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int ra = ab * 8 + a, cb = bb * 8 + 2 * b;
-          if (ra < NN && cb < NN) R[tq * ENT + ra * NN + cb] = acc2[a * 4 + b].x;
-          if (ra < NN && cb + 1 < NN) R[tq * ENT + ra * NN + cb + 1] = acc2[a * 4 + b].y;
-        }
-    } else if (task < n_pq + n_d) {
-      const int k0 = (task - n_pq) * DB;
-#pragma unroll
-      for (int j = 0; j < DB; ++j)
-#pragma unroll
-        for (int c = 0; c < QMAX / 2; ++c) {
-          const float2 v = acc2[j * (QMAX / 2) + c];
-          if (2 * c < Q) Dq[2 * c * DSTRIDE + k0 + j] = v.x;
-          if (2 * c + 1 < Q) Dq[(2 * c + 1) * DSTRIDE + k0 + j] = v.y;
-        }
-    }
-    for (int i = tid; i < Q * NN; i += H27_THREADS) {  // the RHS after the matrix entries
-      const int q = i / NN, a = i - q * NN;
-      R[q * ENT + NN * NN + a] = sm27[L.rhs + i];
+      for (int r = 0; r < 16; r += 4) {
+        *reinterpret_cast<float4*>(d0 + r) = make_float4(acc2[2 * r].x, acc2[2 * r + 2].x, acc2[2 * r + 4].x, acc2[2 * r + 6].x);
+        *reinterpret_cast<float4*>(d0 + DQS + r) =
+            make_float4(acc2[2 * r].y, acc2[2 * r + 2].y, acc2[2 * r + 4].y, acc2[2 * r + 6].y);
+        *reinterpret_cast<float4*>(d0 + 2 * DQS + r) =
+            make_float4(acc2[2 * r + 1].x, acc2[2 * r + 3].x, acc2[2 * r + 5].x, acc2[2 * r + 7].x);
+        *reinterpret_cast<float4*>(d0 + 3 * DQS + r) =
+            make_float4(acc2[2 * r + 1].y, acc2[2 * r + 3].y, acc2[2 * r + 5].y, acc2[2 * r + 7].y);
+      }
     }
     __syncthreads();
     // 9. out
@@ -408,32 +406,39 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
       for (int i = tid; i < Q * NN; i += H27_THREADS) {
         const int q = i / NN, a = i - q * NN;
         const float* fq = p.phi_eval + (int64_t)(p.eq0 + q) * N;
-        const float* Ra = R + q * ENT + a * NN;
-        const float* Dr = Dq + q * DSTRIDE;
+        const float* Ra = R + q * RQ + a * PAD;
         const uint16_t* sa = symt + a * NN;
-        float y = R[q * ENT + NN * NN + a];
+        float y = Ra[NN];
+        const float* Dr = Dq + q * DQS;
         for (int b = 0; b < NN; ++b) y = fmaf(-(Ra[b] + Dr[sa[b]]), fq[ce[b]], y);
         atomicAdd(p.resid + (int64_t)(p.eq0 + q) * N + ce[a], y);
       }
-    } else if (EM) {
+    } else if (EM) {  // em[e][entry][q]: entry a * 27 + b of A, then 729 + a of the RHS
       float* dst = p.em + e * ENT * Q;
       const float invQ = 1.0f / (float)Q;  // i / Q for i < 2^20 as a float quotient (exact here)
       for (int i = tid; i < ENT * Q; i += H27_THREADS) {
         const int ent = (int)(((float)i + 0.5f) * invQ), q = i - ent * Q;
-        float v = R[q * ENT + ent];
-        if (ent < NN * NN) v += Dq[q * DSTRIDE + symt[ent]];
+        float v;
+        if (ent < NN * NN) {
+          const int a = ent / NN, b = ent - a * NN;
+          v = R[q * RQ + a * PAD + b] + Dq[q * DQS + symt[ent]];
+        } else {
+          v = R[q * RQ + (ent - NN * NN) * PAD + NN];
+        }
         dst[i] = v;
       }
-    } else {
+    } else {  // one thread per result slot (a, column), all equations
       const int32_t* pe = reinterpret_cast<const int32_t*>(sm27 + L.spos + cur * NN * NN);
-      for (int ent = tid; ent < ENT; ent += H27_THREADS) {
-        const bool mat = ent < NN * NN;
+      for (int j = tid; j < RQ; j += H27_THREADS) {
+        const int a = j / PAD, b = j - a * PAD;
+        const bool mat = b < NN;
+        const int ent = a * NN + b;
         const int k = mat ? symt[ent] : 0;
-        float* dst = mat ? p.values + (int64_t)p.eq0 * p.nnz + pe[ent] : p.rhs + (int64_t)p.eq0 * N + ce[ent - NN * NN];
+        float* dst = mat ? p.values + (int64_t)p.eq0 * p.nnz + pe[ent] : p.rhs + (int64_t)p.eq0 * N + ce[a];
         const int64_t stride = mat ? p.nnz : N;
         for (int q = 0; q < Q; ++q) {
-          float v = R[q * ENT + ent];
-          if (mat) v += Dq[q * DSTRIDE + k];
+          float v = R[q * RQ + j];
+          if (mat) v += Dq[q * DQS + k];
           atomicAdd(dst + q * stride, v);
         }
       }
@@ -442,12 +447,11 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
   cp_async_wait_all();  // no copy is left in flight when the CTA exits
 }
 
-template <int QMAX>
-fea_status launch_q(const AsmArgs<float>& a, cudaStream_t s) {
+fea_status launch(const AsmArgs<float>& a, cudaStream_t s) {
   const H27Layout L(a.eq_count);
   const size_t smem = sizeof(float) * (size_t)L.total;
   if (smem > 227 * 1024) return fail(FEA_ERR_TOO_LARGE, "hex27 kernel: shared memory");
-  auto kern = a.em ? k_hex27<QMAX, true> : k_hex27<QMAX, false>;
+  auto kern = a.em ? k_hex27<true> : k_hex27<false>;
   FEA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
@@ -463,13 +467,11 @@ fea_status launch_q(const AsmArgs<float>& a, cudaStream_t s) {
 
 }  // namespace
 
-bool hex27_kernel_applies(const AsmArgs<float>& a) { return a.terms == FEA_TERM_ALL && a.eq_count <= 12; }
+bool hex27_kernel_applies(const AsmArgs<float>& a) { return a.terms == FEA_TERM_ALL && a.eq_count <= H27_QMAX; }
 
 fea_status launch_hex27_f32(const AsmArgs<float>& a, cudaStream_t s) {
   if (a.n_elem == 0) return FEA_OK;
-  if (a.eq_count <= 4) return launch_q<4>(a, s);
-  if (a.eq_count <= 8) return launch_q<8>(a, s);
-  return launch_q<12>(a, s);
+  return launch(a, s);
 }
 
 }  // namespace fea
