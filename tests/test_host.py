@@ -75,3 +75,16 @@ def test_generated_meshes_are_valid(t):
     w = G.make_workload(1, n=5, n_eq=1)
     assert O.validate(G.TET4, w.mesh.coords, w.mesh.conn) == O.OK
     assert sorted(np.unique(w.mesh.conn)) == list(range(w.mesh.n_node))
+
+
+def test_oracle_all_cores_timing():
+    """The all-cores CPU baseline: one spawned process per host core, each assembling its own
+    element chunk with the unchanged oracle.  The sub-mesh of all elements is the mesh itself
+    (node renumbering keeps ascending ids), and every process reports a positive rate."""
+    import bench
+    w = G.make_workload(0, n=4)
+    m, f = w.mesh, w.fields
+    coords, conn, arrays = bench._oracle_submesh(m, f, 0, m.n_elem)
+    assert np.array_equal(coords, m.coords) and np.array_equal(conn, m.conn)
+    rates, procs, ne = bench.oracle_all_cores(w, 0.05, 2)
+    assert procs >= 1 and 0 < ne <= m.n_elem and len(rates) == 2 and min(rates) > 0
