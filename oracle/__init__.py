@@ -17,11 +17,11 @@ import threading
 
 import numpy as np
 
-TET4, HEX8, HEX27 = 0, 1, 2
+TET4, HEX8, HEX27, PEN6, PYR5 = 0, 1, 2, 3, 4
 MASS, CONV, DIFF, REAC, SUPG = 1, 2, 4, 8, 16
 ALL_TERMS = 31
 OK, ERR_ARG, ERR_RANGE, ERR_DUP, ERR_INVERTED, ERR_CAP = 0, 1, 2, 3, 4, 5
-NEN = {TET4: 4, HEX8: 8, HEX27: 27}
+NEN = {TET4: 4, HEX8: 8, HEX27: 27, PEN6: 6, PYR5: 5}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fea_oracle.c")
@@ -178,6 +178,43 @@ def assemble(elem_type, coords, conn, rowptr, colind, fields, terms=ALL_TERMS, e
     if with_abs:
         return values, rhs, absA, absb
     return values, rhs
+
+
+def pattern_mixed(blocks, n_node, with_pos=True):
+    """CSR pattern of a mesh made of element blocks [(elem_type, conn), ...] of different types,
+    from its definition (Sec. 4.2: the CSR matrix the element contributions go to): row i holds
+    column j iff some element of any block contains both nodes, columns ascending.  pos is one
+    int32 array [E_b, nen_b, nen_b] per block."""
+    keys = []
+    for t, conn in blocks:
+        c = _c(conn).astype(np.int64)
+        nen = NEN[t]
+        keys.append((np.repeat(c, nen, axis=1) * n_node + np.tile(c, (1, nen))).ravel())
+    key = np.unique(np.concatenate(keys)) if keys else np.zeros(0, np.int64)
+    rows, cols = key // n_node, key % n_node
+    rowptr = np.zeros(n_node + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n_node), out=rowptr[1:])
+    colind = cols.astype(np.int32)
+    pos = None
+    if with_pos:
+        pos = []
+        for t, conn in blocks:
+            c = _c(conn).astype(np.int64)
+            nen = NEN[t]
+            k = c[:, :, None] * n_node + c[:, None, :]
+            pos.append(np.searchsorted(key, k).astype(np.int32).reshape(c.shape[0], nen, nen))
+    return rowptr, colind, pos
+
+
+def assemble_mixed(coords, blocks, rowptr, colind, fields, terms=ALL_TERMS, with_abs=False):
+    """Assembly of a mesh of element blocks: the sum of every block's element contributions."""
+    outs = [assemble(t, coords, conn, rowptr, colind, fields, terms, with_abs=with_abs) for t, conn in blocks]
+    return tuple(sum(o[i] for o in outs) for i in range(len(outs[0])))
+
+
+def apply_mixed(coords, blocks, fields, q, x, terms=ALL_TERMS):
+    """Matrix-free A x of a mesh of element blocks, summed over the blocks."""
+    return sum(apply(t, coords, conn, fields, q, x, terms) for t, conn in blocks)
 
 
 class RowSampler:

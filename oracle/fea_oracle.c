@@ -13,6 +13,13 @@
  *     elements, inner loop over Gauss points and node pairs, Ae(a,b) +=
  *     Jac(g) N(a,g) N(b,g).  Jac(g) is read as w_g * det J_g.
  *   - Sec. 4.2: the global matrix is stored in CSR.
+ *   - Sec. 2 and Sec. 4.2: the meshes are unstructured and mix element kinds
+ *     (tetrahedra, prisms, pyramids, hexahedra).  Element types here: Tet4,
+ *     Hex8, Hex27, Pen6 (linear prism: triangle x line) and Pyr5 (linear
+ *     pyramid with rational base functions, integrated on a collapsed cube).
+ *     The paper gives no shape functions or rules; these are textbook ones.
+ *     A mesh of several types is a list of single-type blocks (the Python
+ *     wrapper sums their contributions into one CSR pattern).
  *   - Sec. 2: heat and species transport equations assembled every step.
  *     The paper does not write these equations; the operator used is the
  *     backward-Euler Galerkin + SUPG discretisation of
@@ -37,7 +44,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { OR_TET4 = 0, OR_HEX8 = 1, OR_HEX27 = 2 };
+enum { OR_TET4 = 0, OR_HEX8 = 1, OR_HEX27 = 2, OR_PEN6 = 3, OR_PYR5 = 4 };
 enum { OR_MASS = 1, OR_CONV = 2, OR_DIFF = 4, OR_REAC = 8, OR_SUPG = 16, OR_ALL = 31 };
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_RANGE = 2, OR_ERR_DUP = 3, OR_ERR_INVERTED = 4, OR_ERR_CAP = 5 };
 
@@ -73,7 +80,9 @@ static void lagrange1d(int order, int i, double t, double* val, double* der) {
   *der = d;
 }
 
-int or_nen(int type) { return type == OR_TET4 ? 4 : type == OR_HEX8 ? 8 : type == OR_HEX27 ? 27 : 0; }
+int or_nen(int type) {
+  return type == OR_TET4 ? 4 : type == OR_HEX8 ? 8 : type == OR_HEX27 ? 27 : type == OR_PEN6 ? 6 : type == OR_PYR5 ? 5 : 0;
+}
 int or_order(int type) { return type == OR_HEX27 ? 2 : 1; }
 
 /* Shape functions N[a] and reference derivatives dN[a][j] = dN_a/dxi_j at xi. */
@@ -86,6 +95,41 @@ int or_shape(int type, const double* xi, double* N, double* dN) {
     for (int a = 0; a < 4; ++a)
       for (int j = 0; j < 3; ++j) dN[a * 3 + j] = (a == 0) ? -1.0 : (a - 1 == j ? 1.0 : 0.0);
     return 4;
+  }
+  if (type == OR_PEN6) {
+    /* prism: linear triangle in (xi, eta) times linear in zeta on [-1, 1]; node i + 3k is
+     * triangle vertex i ((0,0), (1,0), (0,1)) on the face zeta = -1 (k = 0) or +1 (k = 1) */
+    double L[3] = {1.0 - xi[0] - xi[1], xi[0], xi[1]};
+    if (g_mutation == 13) { double t = L[0]; L[0] = L[1]; L[1] = t; }
+    const double dLx[3] = {-1.0, 1.0, 0.0}, dLy[3] = {-1.0, 0.0, 1.0};
+    const double l[2] = {0.5 * (1.0 - xi[2]), 0.5 * (1.0 + xi[2])}, dl[2] = {-0.5, 0.5};
+    for (int k = 0; k < 2; ++k)
+      for (int i = 0; i < 3; ++i) {
+        int a = i + 3 * k;
+        N[a] = L[i] * l[k];
+        dN[a * 3 + 0] = dLx[i] * l[k];
+        dN[a * 3 + 1] = dLy[i] * l[k];
+        dN[a * 3 + 2] = L[i] * dl[k];
+      }
+    return 6;
+  }
+  if (type == OR_PYR5) {
+    /* pyramid: square base [-1,1]^2 at zeta = 0 with corners (xi_a, eta_a) = (-1,-1), (1,-1),
+     * (1,1), (-1,1), apex (0,0,1).  Base functions (1/4) [(1 - zeta) + xi_a xi + eta_a eta +
+     * xi_a eta_a xi eta / (1 - zeta)], apex function zeta (rational, defined for zeta < 1). */
+    const double sx[4] = {-1.0, 1.0, 1.0, -1.0}, sy[4] = {-1.0, -1.0, 1.0, 1.0};
+    const double x = xi[0], y = xi[1], z = xi[2], c = 1.0 - z;
+    for (int a = 0; a < 4; ++a) {
+      N[a] = 0.25 * (c + sx[a] * x + sy[a] * y + sx[a] * sy[a] * x * y / c);
+      dN[a * 3 + 0] = 0.25 * (sx[a] + sx[a] * sy[a] * y / c);
+      dN[a * 3 + 1] = 0.25 * (sy[a] + sx[a] * sy[a] * x / c);
+      dN[a * 3 + 2] = 0.25 * (-1.0 + sx[a] * sy[a] * x * y / (c * c));
+    }
+    N[4] = z;
+    dN[12] = 0.0;
+    dN[13] = 0.0;
+    dN[14] = 1.0;
+    return 5;
   }
   if (type != OR_HEX8 && type != OR_HEX27) return 0;
   int order = or_order(type), q = order + 1;
@@ -120,6 +164,39 @@ int or_quadrature(int type, double* xi, double* w) {
     }
     return 4;
   }
+  if (type == OR_PEN6) {
+    /* triangle rule of degree 2 (points (1/6,1/6), (2/3,1/6), (1/6,2/3), weight 1/6 each)
+     * times 2-point Gauss-Legendre in zeta; point t + 3k */
+    const double tp[3][2] = {{1.0 / 6.0, 1.0 / 6.0}, {2.0 / 3.0, 1.0 / 6.0}, {1.0 / 6.0, 2.0 / 3.0}};
+    const double zp[2] = {-1.0 / sqrt(3.0), 1.0 / sqrt(3.0)};
+    for (int k = 0; k < 2; ++k)
+      for (int t = 0; t < 3; ++t) {
+        int g = t + 3 * k;
+        xi[g * 3 + 0] = tp[t][0];
+        xi[g * 3 + 1] = tp[t][1];
+        xi[g * 3 + 2] = zp[k];
+        w[g] = 1.0 / 6.0;
+      }
+    return 6;
+  }
+  if (type == OR_PYR5) {
+    /* collapsed cube: xi = r (1 - zeta), eta = s (1 - zeta), dxi deta dzeta = (1 - zeta)^2 dr ds
+     * dzeta; 2-point Gauss-Legendre in r and s, 3-point Gauss-Legendre in zeta mapped to [0, 1];
+     * point i + 2j + 4k (r fastest) */
+    const double rp[2] = {-1.0 / sqrt(3.0), 1.0 / sqrt(3.0)};
+    const double zt[3] = {-sqrt(0.6), 0.0, sqrt(0.6)}, zw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
+    for (int k = 0; k < 3; ++k)
+      for (int j = 0; j < 2; ++j)
+        for (int i = 0; i < 2; ++i) {
+          int g = i + 2 * j + 4 * k;
+          double z = 0.5 * (1.0 + zt[k]), c = 1.0 - z;
+          xi[g * 3 + 0] = rp[i] * c;
+          xi[g * 3 + 1] = rp[j] * c;
+          xi[g * 3 + 2] = z;
+          w[g] = 0.5 * zw[k] * (g_mutation == 12 ? 1.0 : c * c);
+        }
+    return 12;
+  }
   double p[3], pw[3];
   int q;
   if (type == OR_HEX8) {
@@ -145,10 +222,21 @@ int or_quadrature(int type, double* xi, double* w) {
   return g;
 }
 
-/* Reference corner points used by the orientation check. */
+/* Reference corner points used by the orientation check (the pyramid's base corners only:
+ * its rational functions are singular at the apex). */
 static int corner_points(int type, double* xi) {
   if (type == OR_TET4) {
     const double c[4][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    memcpy(xi, c, sizeof(c));
+    return 4;
+  }
+  if (type == OR_PEN6) {
+    const double c[6][3] = {{0, 0, -1}, {1, 0, -1}, {0, 1, -1}, {0, 0, 1}, {1, 0, 1}, {0, 1, 1}};
+    memcpy(xi, c, sizeof(c));
+    return 6;
+  }
+  if (type == OR_PYR5) {
+    const double c[4][3] = {{-1, -1, 0}, {1, -1, 0}, {1, 1, 0}, {-1, 1, 0}};
     memcpy(xi, c, sizeof(c));
     return 4;
   }

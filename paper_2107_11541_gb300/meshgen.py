@@ -16,6 +16,14 @@ Meshes
   ``(i,j,k)``.
 * Hex27: element ``(ex,ey,ez)`` owns grid nodes ``(2ex+i, 2ey+j, 2ez+k)``,
   local node ``a = i + 3j + 9k``.
+* Pen6: each cube is split into two prisms whose triangles lie in x = const planes
+  (cut along the diagonal from (y1, z0) to (y0, z1)) and are extruded along x;
+  local nodes 0-2 on the face x0, 3-5 the same vertices on x1.
+* Pyr5: each cube gets a centre node (ids after the grid nodes) and is split into
+  six pyramids, one per face, base corners counter-clockwise seen from the centre
+  (the apex, local node 4).
+* Mixed: the cells with k < n/3 are Hex8, n/3 <= k < 2n/3 Pyr5, the rest Pen6; the
+  interfaces between the layers are the quads of all three types.
 
 Fields
 ------
@@ -34,9 +42,9 @@ import itertools
 
 import numpy as np
 
-TET4, HEX8, HEX27 = 0, 1, 2
-NEN = {TET4: 4, HEX8: 8, HEX27: 27}
-NAMES = {TET4: "tet4", HEX8: "hex8", HEX27: "hex27"}
+TET4, HEX8, HEX27, PEN6, PYR5 = 0, 1, 2, 3, 4
+NEN = {TET4: 4, HEX8: 8, HEX27: 27, PEN6: 6, PYR5: 5}
+NAMES = {TET4: "tet4", HEX8: "hex8", HEX27: "hex27", PEN6: "pen6", PYR5: "pyr5"}
 SEED_BASE = 11541
 DT = 1e-3
 
@@ -117,15 +125,93 @@ def hex_conn(n: int, order: int) -> np.ndarray:
     return (base[:, None] + np.asarray(offs, dtype=np.int64)[None, :]).astype(np.int32)
 
 
+# grid offsets (dx, dy, dz) of the two prisms of a cube and of the six pyramid bases
+PRISMS = (((0, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 0), (1, 1, 0), (1, 0, 1)),
+          ((0, 1, 0), (0, 1, 1), (0, 0, 1), (1, 1, 0), (1, 1, 1), (1, 0, 1)))
+PYRAMID_BASES = (((0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0)),   # z0, inward normal +z
+                 ((0, 0, 1), (0, 1, 1), (1, 1, 1), (1, 0, 1)),   # z1
+                 ((0, 0, 0), (0, 0, 1), (1, 0, 1), (1, 0, 0)),   # y0
+                 ((0, 1, 0), (1, 1, 0), (1, 1, 1), (0, 1, 1)),   # y1
+                 ((0, 0, 0), (0, 1, 0), (0, 1, 1), (0, 0, 1)),   # x0
+                 ((1, 0, 0), (1, 0, 1), (1, 1, 1), (1, 1, 0)))   # x1
+
+
+def _offsets(m: int, pts) -> np.ndarray:
+    return np.asarray([dx + m * dy + m * m * dz for dx, dy, dz in pts], dtype=np.int64)
+
+
+def prism_conn(base: np.ndarray, m: int) -> np.ndarray:
+    conn = np.stack([base[:, None] + _offsets(m, p)[None, :] for p in PRISMS], axis=1)
+    return conn.reshape(-1, 6).astype(np.int32)
+
+
+def pyramid_conn(base: np.ndarray, m: int, centre: np.ndarray) -> np.ndarray:
+    conn = np.empty((base.size, 6, 5), dtype=np.int64)
+    for f, quad in enumerate(PYRAMID_BASES):
+        conn[:, f, :4] = base[:, None] + _offsets(m, quad)[None, :]
+        conn[:, f, 4] = centre
+    return conn.reshape(-1, 5).astype(np.int32)
+
+
+def cell_centres(n: int, cells: np.ndarray) -> np.ndarray:
+    """Centres of the cells with the given indices (k slowest) of the n^3 grid on [0,1]^3."""
+    k, rem = np.divmod(cells, n * n)
+    j, i = np.divmod(rem, n)
+    return (np.stack([i, j, k], axis=1) + 0.5) / n
+
+
 def structured_mesh(elem_type: int, n: int, z_faces: np.ndarray | None = None) -> Mesh:
     order = 2 if elem_type == HEX27 else 1
     m = order * n + 1
     coords = grid_nodes(m, z_faces)
     if elem_type == TET4:
         conn = kuhn_tets(n)
+    elif elem_type == PEN6:
+        conn = prism_conn(_cell_origins(n, m, 1), m)
+    elif elem_type == PYR5:
+        cells = np.arange(n ** 3)
+        conn = pyramid_conn(_cell_origins(n, m, 1), m, m ** 3 + cells)
+        coords = np.concatenate([coords, cell_centres(n, cells)])
     else:
         conn = hex_conn(n, order)
     return Mesh(elem_type, coords, conn, n, 1.0 / n)
+
+
+@dataclasses.dataclass
+class MixedMesh:
+    """A mesh of element blocks of different types sharing one node set."""
+    coords: np.ndarray   # (N, 3) float64
+    blocks: list         # [(elem_type, conn (E_b, nen_b) int32)]
+    n_cells: int
+    h: float
+
+    @property
+    def n_node(self) -> int:
+        return int(self.coords.shape[0])
+
+    @property
+    def n_elem(self) -> int:
+        return int(sum(c.shape[0] for _, c in self.blocks))
+
+
+def mixed_mesh(n: int) -> MixedMesh:
+    """Unit cube, n^3 cells: Hex8 cells below z = 1/3, Pyr5 cells (six pyramids around a
+    centre node) up to z = 2/3, Pen6 cells (two prisms) above; n >= 3."""
+    if n < 3:
+        raise ValueError("a mixed mesh needs n >= 3 cells per axis")
+    m = n + 1
+    base = _cell_origins(n, m, 1)
+    k1, k2 = n // 3, (2 * n) // 3
+    hexes = base[: k1 * n * n]
+    pyr_cells = np.arange(k1 * n * n, k2 * n * n)
+    prisms = base[k2 * n * n:]
+    centres = cell_centres(n, pyr_cells)
+    coords = np.concatenate([grid_nodes(m), centres])
+    blocks = [(HEX8, (hexes[:, None] + _offsets(m, [(i, j, k) for k in range(2) for j in range(2)
+                                                    for i in range(2)])[None, :]).astype(np.int32)),
+              (PYR5, pyramid_conn(base[pyr_cells], m, m ** 3 + np.arange(pyr_cells.size))),
+              (PEN6, prism_conn(prisms, m))]
+    return MixedMesh(coords, blocks, n, 1.0 / n)
 
 
 def interior_mask(mesh: Mesh) -> np.ndarray:

@@ -17,14 +17,19 @@ from numpy.polynomial import polynomial as P
 import oracle as O
 from paper_2107_11541_gb300 import meshgen as G
 
-TYPES = (O.TET4, O.HEX8, O.HEX27)
-REF_VOLUME = {O.TET4: 1.0 / 6.0, O.HEX8: 8.0, O.HEX27: 8.0}
+TYPES = (O.TET4, O.HEX8, O.HEX27, O.PEN6, O.PYR5)
+REF_VOLUME = {O.TET4: 1.0 / 6.0, O.HEX8: 8.0, O.HEX27: 8.0, O.PEN6: 1.0, O.PYR5: 4.0 / 3.0}
 
 
 def ref_nodes(t):
-    """Reference coordinates of the nodes in the documented local order."""
+    """Reference coordinates of the nodes in the documented local order (the pyramid's apex
+    a hair below z = 1, where its rational functions are singular)."""
     if t == O.TET4:
         return np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    if t == O.PEN6:
+        return np.array([[0, 0, -1], [1, 0, -1], [0, 1, -1], [0, 0, 1], [1, 0, 1], [0, 1, 1]], float)
+    if t == O.PYR5:
+        return np.array([[-1, -1, 0], [1, -1, 0], [1, 1, 0], [-1, 1, 0], [0, 0, 1 - 1e-15]], float)
     q = 2 if t == O.HEX8 else 3
     pts = np.linspace(-1, 1, q)
     return np.array([[pts[i], pts[j], pts[k]] for k in range(q) for j in range(q) for i in range(q)])
@@ -42,6 +47,21 @@ def check_quadrature(t):
                     exact = math.factorial(a) * math.factorial(b) * math.factorial(c) / math.factorial(a + b + c + 3)
                     got = np.sum(w * xi[:, 0] ** a * xi[:, 1] ** b * xi[:, 2] ** c)
                     assert abs(got - exact) < 1e-15
+    elif t == O.PEN6:  # triangle degree 2 x line degree 3: int x^a y^b = a! b! / (a+b+2)!, int z^c = 2/(c+1)
+        for a in range(3):
+            for b in range(3 - a):
+                for c in range(4):
+                    tri = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+                    exact = tri * (2.0 / (c + 1) if c % 2 == 0 else 0.0)
+                    got = np.sum(w * xi[:, 0] ** a * xi[:, 1] ** b * xi[:, 2] ** c)
+                    assert abs(got - exact) < 1e-14
+    elif t == O.PYR5:  # int over |x|,|y| <= 1-z: I_a I_b c! (a+b+2)! / (a+b+c+3)!, I_a = 2/(a+1) (a even)
+        for a, b, c in ((a, b, c) for a in range(4) for b in range(4) for c in range(4) if a + b + c <= 3):
+            ia = 2.0 / (a + 1) if a % 2 == 0 else 0.0
+            ib = 2.0 / (b + 1) if b % 2 == 0 else 0.0
+            exact = ia * ib * math.factorial(c) * math.factorial(a + b + 2) / math.factorial(a + b + c + 3)
+            got = np.sum(w * xi[:, 0] ** a * xi[:, 1] ** b * xi[:, 2] ** c)
+            assert abs(got - exact) < 1e-14
     else:  # Gauss-Legendre with n points per axis is exact to degree 2n-1 per axis
         deg = 3 if t == O.HEX8 else 5
         for a in range(deg + 1):
@@ -58,7 +78,15 @@ def check_shape_functions(t, rng):
         N, _ = O.shape(t, x)
         assert np.allclose(N, np.eye(len(nodes))[b], atol=1e-14)
     for _ in range(5):
-        x = rng.uniform(0, 0.3, 3) if t == O.TET4 else rng.uniform(-1, 1, 3)
+        if t == O.TET4:
+            x = rng.uniform(0, 0.3, 3)
+        elif t == O.PEN6:
+            x = np.array([rng.uniform(0, 0.45), rng.uniform(0, 0.45), rng.uniform(-1, 1)])
+        elif t == O.PYR5:
+            z = rng.uniform(0, 0.8)
+            x = np.array([rng.uniform(-0.9, 0.9) * (1 - z), rng.uniform(-0.9, 0.9) * (1 - z), z])
+        else:
+            x = rng.uniform(-1, 1, 3)
         N, dN = O.shape(t, x)
         assert abs(N.sum() - 1.0) < 1e-14  # partition of unity
         assert np.allclose(dN.sum(axis=0), 0.0, atol=1e-13)
@@ -213,7 +241,7 @@ def csr(mesh, fields, terms):
     return A, rhs[0]
 
 
-INV_MESH = {O.TET4: (3, 0.2), O.HEX8: (3, 0.15), O.HEX27: (2, 0.1)}
+INV_MESH = {O.TET4: (3, 0.2), O.HEX8: (3, 0.15), O.HEX27: (2, 0.1), O.PEN6: (3, 0.15), O.PYR5: (3, 0.15)}
 
 
 def check_invariants(t):
@@ -294,55 +322,74 @@ def test_scaling_translation(t):
 
 # ------------------------------------------------------------------ patch test
 
-def boundary_faces(mesh):
-    """(node list, reference-face kind) of every boundary face of a structured unit-cube mesh."""
-    t = mesh.elem_type
-    if t == O.TET4:
-        faces = {}
-        for e in mesh.conn:
-            for f in ((0, 1, 2), (0, 1, 3), (0, 2, 3), (1, 2, 3)):
-                key = tuple(sorted(e[list(f)]))
-                faces[key] = faces.get(key, 0) + 1
-        return [list(k) for k, c in faces.items() if c == 1]
-    q = 2 if t == O.HEX8 else 3
+# local faces: triangles as 3 nodes, quads as 2 x 2 arrays (tensor layout of the face's bilinear basis)
+LOCAL_FACES = {
+    O.TET4: [[0, 1, 2], [0, 1, 3], [0, 2, 3], [1, 2, 3]],
+    O.PEN6: [[0, 1, 2], [3, 4, 5], [[0, 1], [3, 4]], [[1, 2], [4, 5]], [[2, 0], [5, 3]]],
+    O.PYR5: [[[0, 1], [3, 2]], [0, 1, 4], [1, 2, 4], [2, 3, 4], [3, 0, 4]],
+}
+
+
+def on_cube_boundary(x):
+    return any(np.all(np.abs(x[:, d] - v) < 1e-12) for d in range(3) for v in (0.0, 1.0))
+
+
+def boundary_faces_of(t, conn, coords):
+    """Node arrays of the faces of elements of type t that lie on the boundary of the unit cube."""
     out = []
-    for e in mesh.conn:
+    if t in LOCAL_FACES:
+        for e in conn:
+            for f in LOCAL_FACES[t]:
+                nodes = e[np.asarray(f)]
+                if on_cube_boundary(coords[nodes.ravel()]):
+                    out.append(nodes)
+        return out
+    q = 2 if t == O.HEX8 else 3
+    for e in conn:
         loc = e.reshape(q, q, q)  # [k][j][i]
         for sl in (loc[0], loc[-1], loc[:, 0, :], loc[:, -1, :], loc[:, :, 0], loc[:, :, -1]):
-            x = mesh.coords[sl.ravel()]
-            on = [np.all(np.abs(x[:, d] - v) < 1e-12) for d in range(3) for v in (0.0, 1.0)]
-            if any(on):
+            if on_cube_boundary(coords[sl.ravel()]):
                 out.append(sl)
     return out
 
 
-def boundary_flux(mesh, kval, g):
-    """f_i = int_dOmega N_i k g.n on the planar faces of the unit cube."""
-    f = np.zeros(mesh.n_node)
-    for face in boundary_faces(mesh):
-        nodes = np.asarray(face).ravel()
-        x = mesh.coords[nodes]
-        c = x.mean(axis=0)
+def boundary_faces(mesh):
+    return boundary_faces_of(mesh.elem_type, mesh.conn, mesh.coords)
+
+
+def boundary_flux_faces(faces, coords, n_node, kval, g):
+    """f_i = int_dOmega N_i k g.n over planar boundary faces of the unit cube: a linear triangle
+    gives each vertex a third of its area; a flat rectangle with the tensor basis of 2 or 3
+    nodes per side takes the trapezoid or Simpson weights, which integrate it exactly."""
+    f = np.zeros(n_node)
+    for face in faces:
+        arr = np.asarray(face)
+        nodes = arr.ravel()
+        x = coords[nodes]
         d = [d for d in range(3) if np.all(np.abs(x[:, d] - x[0, d]) < 1e-12)][0]
         n = np.zeros(3)
         n[d] = 1.0 if x[0, d] > 0.5 else -1.0
-        if mesh.elem_type == O.TET4:
+        if arr.ndim == 1:
             area = 0.5 * np.linalg.norm(np.cross(x[1] - x[0], x[2] - x[0]))
             w = np.full(3, area / 3.0)
         else:
-            arr = np.asarray(face)
             q = arr.shape[0]
             ext = [np.ptp(x[:, dd]) for dd in range(3) if dd != d]
             area = ext[0] * ext[1]
-            # Simpson (q=3) or trapezoid (q=2) weights integrate the face basis exactly on a flat rectangle
             w1 = np.array([0.5, 0.5]) if q == 2 else np.array([1.0, 4.0, 1.0]) / 6.0
             w = (np.outer(w1, w1) * area).ravel()
-        del c
         f[nodes] += kval * (g @ n) * w
     return f
 
 
-@pytest.mark.parametrize("t,frac", [(O.TET4, 0.2), (O.HEX8, 0.15), (O.HEX27, 0.0)])
+def boundary_flux(mesh, kval, g):
+    return boundary_flux_faces(boundary_faces(mesh), mesh.coords, mesh.n_node, kval, g)
+
+
+PATCH = [(O.TET4, 0.2), (O.HEX8, 0.15), (O.HEX27, 0.0), (O.PEN6, 0.15), (O.PYR5, 0.0)]
+
+
+@pytest.mark.parametrize("t,frac", PATCH)
 def test_patch_test(t, frac):
     check_patch(t, frac)
 
@@ -496,6 +543,67 @@ def test_validation_codes():
     assert O.validate(O.HEX8, h.coords, bad) == O.ERR_INVERTED
 
 
+# ------------------------------------------------------------------ mixed element types
+
+def check_mixed():
+    """A mesh of Hex8, Pyr5 and Pen6 blocks: its pattern is the incidence product over all
+    blocks; the mass matrix sums to the cube's volume; diffusion and convection annihilate
+    constants; the constant state is preserved; the patch test holds against the boundary
+    flux of all blocks' faces; matrix-free equals SpMV."""
+    mm = G.mixed_mesh(3)
+    G.perturb_interior(mm, np.random.default_rng(4), 0.1)
+    N = mm.n_node
+    rp, ci, pos = O.pattern_mixed(mm.blocks, N)
+    inc = np.zeros((N, mm.n_elem))
+    e0 = 0
+    for t, conn in mm.blocks:
+        for i, e in enumerate(conn):
+            inc[e, e0 + i] = 1.0
+        e0 += conn.shape[0]
+    S = (inc @ inc.T) > 0
+    P_ = np.zeros((N, N), bool)
+    for r in range(N):
+        P_[r, ci[rp[r]:rp[r + 1]]] = True
+    assert np.array_equal(S, P_)
+    for (t, conn), pb in zip(mm.blocks, pos):
+        assert np.array_equal(ci[pb], np.broadcast_to(conn[:, None, :], pb.shape))
+    rng = np.random.default_rng(8)
+    f = G.Fields(G.velocity_field(mm.coords), rng.uniform(0.01, 0.1, (1, N)), rng.uniform(0, 5, (1, N)),
+                 rng.uniform(0, 1, (1, N)), 1e-3)
+
+    def mat(fields, terms):
+        v, b = O.assemble_mixed(mm.coords, mm.blocks, rp, ci, fields, terms)
+        return sp.csr_matrix((v[0], ci, rp), shape=(N, N)), b[0]
+
+    one = np.ones(N)
+    M, _ = mat(f, O.MASS)
+    assert abs(M.sum() / (1.0 / f.dt) - 1.0) < 1e-12
+    for terms in (O.DIFF, O.CONV):
+        A, _ = mat(f, terms)
+        assert np.abs(A @ one).max() < 1e-12 * abs(A).max()
+    fc = G.Fields(f.velocity, f.diffusivity, np.zeros((1, N)), np.ones((1, N)), f.dt)
+    A, b = mat(fc, O.ALL_TERMS)
+    assert np.abs(A @ one - b).max() < 1e-11 * np.abs(b).max()
+    x = rng.standard_normal(N)
+    A, _ = mat(f, O.ALL_TERMS)
+    y = O.apply_mixed(mm.coords, mm.blocks, f, 0, x)
+    assert np.abs(A @ x - y).max() < 1e-12 * np.abs(y).max()
+    # patch test on the unperturbed mesh (the pyramids' rational functions are integrated exactly there)
+    flat = G.mixed_mesh(3)
+    rpf, cif, _ = O.pattern_mixed(flat.blocks, flat.n_node, with_pos=False)
+    g, kval = np.array([0.7, -0.4, 1.3]), 0.3
+    ff = const_fields(flat.n_node, flat.coords, k=kval)
+    v, _ = O.assemble_mixed(flat.coords, flat.blocks, rpf, cif, ff, O.DIFF)
+    K = sp.csr_matrix((v[0], cif, rpf), shape=(flat.n_node, flat.n_node))
+    faces = [fc_ for t, conn in flat.blocks for fc_ in boundary_faces_of(t, conn, flat.coords)]
+    want = boundary_flux_faces(faces, flat.coords, flat.n_node, kval, g)
+    assert np.abs(K @ (flat.coords @ g + 0.25) - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_mixed_element_types():
+    check_mixed()
+
+
 # ------------------------------------------------------------------ planted mistakes
 
 def all_pins():
@@ -507,8 +615,8 @@ def all_pins():
                  lambda t=t: check_scaling_translation(t)]
     pins += [lambda: check_box_closed_forms(O.HEX8), lambda: check_box_closed_forms(O.HEX27),
              lambda: check_tet_closed_forms(np.random.default_rng(7)), check_pattern_counts,
-             lambda: check_patch(O.TET4, 0.2), lambda: check_patch(O.HEX8, 0.15), lambda: check_patch(O.HEX27, 0.0),
-             lambda: check_bruteforce(O.HEX8)]
+             lambda: check_bruteforce(O.HEX8), check_mixed]
+    pins += [lambda t=t, fr=fr: check_patch(t, fr) for t, fr in PATCH]
     return pins
 
 
@@ -548,6 +656,8 @@ MUTATIONS = {
     9: "element matrix scattered transposed",
     10: "mass term uses N_a N_a",
     11: "quadratic 1-D nodes in the wrong order",
+    12: "pyramid rule without the collapse factor (1 - zeta)^2",
+    13: "prism triangle functions permuted, derivatives not",
 }
 
 
