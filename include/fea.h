@@ -29,7 +29,18 @@
  *     fea_last_error() returns a thread-local message.
  *   - Node ids are 0-based int32.  Local node order: Tet4 positively oriented
  *     ((x1-x0)x(x2-x0).(x3-x0) > 0); Hex8 a = i + 2j + 4k and Hex27
- *     a = i + 3j + 9k, with i, j, k the node's position along xi, eta, zeta.
+ *     a = i + 3j + 9k, with i, j, k the node's position along xi, eta, zeta;
+ *     Pen6 (prism) nodes 0-2 a triangle and 3-5 the opposite triangle, node
+ *     a + 3 across from node a, with (x1-x0)x(x2-x0).(x3-x0) > 0; Pyr5
+ *     (pyramid) nodes 0-3 the base quad counter-clockwise seen from the apex,
+ *     node 4 the apex.
+ *   - Element types and Gauss rules (Sec. 2 and Sec. 4.2: unstructured meshes
+ *     mixing tetrahedra, prisms, pyramids and hexahedra; the paper gives no
+ *     rules): Tet4 4 points (degree 2); Hex8 2x2x2 and Hex27 3x3x3 Gauss;
+ *     Pen6 linear triangle x linear line, 3 x 2 points; Pyr5 rational base
+ *     functions (1/4)[(1-z) + xa x + ya y + xa ya x y/(1-z)] and apex z on the
+ *     reference pyramid |x|,|y| <= 1-z, 0 <= z <= 1, 2x2x3 points of a cube
+ *     collapsed onto it.  h = V_e^(1/3) / p with p = 2 for Hex27, else 1.
  *   - Device work is ordered on the mesh's CUDA stream.  Calls that only
  *     enqueue work return without waiting; device-detected errors are
  *     reported by the next call that waits (fea_sync, fea_pattern_build,
@@ -55,7 +66,7 @@ typedef struct fea_mesh fea_mesh;
 typedef struct fea_pattern fea_pattern;
 typedef struct fea_graph fea_graph;
 
-typedef enum { FEA_TET4 = 0, FEA_HEX8 = 1, FEA_HEX27 = 2 } fea_elem_t;
+typedef enum { FEA_TET4 = 0, FEA_HEX8 = 1, FEA_HEX27 = 2, FEA_PEN6 = 3, FEA_PYR5 = 4 } fea_elem_t;
 
 typedef enum {
   FEA_OK = 0,
@@ -131,6 +142,26 @@ FEA_API fea_status fea_default_opts(fea_assemble_opts* opts);
  */
 FEA_API fea_status fea_mesh_create(const double* coords, int64_t n_node, const int32_t* conn, int64_t n_elem,
                            fea_elem_t type, void* stream, fea_mesh** out);
+
+/*
+ * fea_mesh_create_mixed -- a mesh of n_blocks element blocks of different types sharing
+ * one node set (Sec. 2 and Sec. 4.2: one unstructured mesh of several element kinds;
+ * elements grouped by type as in Sec. 4.3).
+ *   coords       [n_node][3] double, host or device pointer, copied.
+ *   types[b]     element type of block b (host array of n_blocks).
+ *   conns[b]     [n_elems[b]][nen of types[b]] int32, host or device pointer, copied
+ *                (host array of n_blocks pointers; may be NULL where n_elems[b] = 0).
+ *   n_elems[b]   elements of block b (host array).
+ * Elements are numbered block by block.  Validation as in fea_mesh_create, per block.
+ * n_blocks = 1 gives the single-type mesh of fea_mesh_create.  On a mesh of several
+ * types the position map of fea_pattern_get holds block b's [n_elems[b]][nen_b][nen_b]
+ * array after those of blocks 0..b-1; fea_assemble scatters with atomics (AUTO or
+ * ATOMIC; ROWOWNED, GATHER and the cancellation check return FEA_ERR_ARG); fea_residual,
+ * fea_assemble_host, fea_spmv and the step graph work as on any mesh.
+ */
+FEA_API fea_status fea_mesh_create_mixed(const double* coords, int64_t n_node, int32_t n_blocks,
+                                         const fea_elem_t* types, const int32_t* const* conns,
+                                         const int64_t* n_elems, void* stream, fea_mesh** out);
 FEA_API fea_status fea_mesh_destroy(fea_mesh* mesh);
 /* Rebinds the mesh (and its patterns) to another stream. */
 FEA_API fea_status fea_mesh_set_stream(fea_mesh* mesh, void* stream);
@@ -147,7 +178,8 @@ FEA_API fea_status fea_sync(fea_mesh* mesh);
  * nnz >= 2^31.  Waits for the stream.
  */
 FEA_API fea_status fea_pattern_build(fea_mesh* mesh, fea_pattern** out);
-/* Borrowed device pointers: rowptr int64[n_node+1], colind int32[nnz], pos int32[n_elem][nen][nen]. */
+/* Borrowed device pointers: rowptr int64[n_node+1], colind int32[nnz], pos int32[n_elem][nen][nen]
+ * (on a mesh of several types: every block's array in turn, see fea_mesh_create_mixed). */
 FEA_API fea_status fea_pattern_get(const fea_pattern* pattern, const int64_t** rowptr, const int32_t** colind,
                            const int32_t** pos, int64_t* nnz);
 FEA_API fea_status fea_pattern_destroy(fea_pattern* pattern);

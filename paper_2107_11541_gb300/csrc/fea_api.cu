@@ -217,9 +217,10 @@ __global__ void k_split_coords(const double* __restrict__ coords, int64_t n_node
 
 // ------------------------------------------------------------------ pattern kernels
 
+// Connectivity slots below 0 are the padding of a mesh of several element types.
 __global__ void k_inc_count(const int32_t* __restrict__ conn, int64_t total, int32_t* cnt) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < total) atomicAdd(&cnt[conn[t]], 1);
+  if (t < total && conn[t] >= 0) atomicAdd(&cnt[conn[t]], 1);
 }
 
 __global__ void k_inc_fill(const int32_t* __restrict__ conn, int64_t total, int nen, const int64_t* inc_ptr,
@@ -227,6 +228,7 @@ __global__ void k_inc_fill(const int32_t* __restrict__ conn, int64_t total, int 
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= total) return;
   int32_t n = conn[t];
+  if (n < 0) return;
   int32_t k = atomicAdd(&cursor[n], 1);
   inc_elem[inc_ptr[n] + k] = (int32_t)(t / nen);
 }
@@ -288,6 +290,7 @@ k_rows(const int32_t* __restrict__ conn, int nen, const int64_t* __restrict__ in
       if (i < cnt) {
         int64_t t = i0 + i / nen;
         v = conn[(int64_t)inc_elem[t] * nen + (i % nen)];
+        if (v < 0) v = INT_MAX;  // padding slot: sorts last, never a column
       }
       s[i] = v;
     }
@@ -297,7 +300,7 @@ k_rows(const int32_t* __restrict__ conn, int nen, const int64_t* __restrict__ in
     int64_t written = 0;
     for (int base = 0; base < cnt; base += 32) {
       int i = base + lane;
-      bool first = i < cnt && (i == 0 || s[i] != s[i - 1]);
+      bool first = i < cnt && s[i] != INT_MAX && (i == 0 || s[i] != s[i - 1]);
       unsigned m = __ballot_sync(0xffffffffu, first);
       if (mode == 1 && first) {
         int off = __popc(m & ((1u << lane) - 1u));
@@ -372,7 +375,18 @@ static fea_status check_assemble_args(fea_mesh* m, const fea_pattern* p, const v
     return fail(FEA_ERR_ARG, "the gather scatter is an FP32 path");
   if (o->cancel_check != 0 && o->cancel_check != 1) return fail(FEA_ERR_ARG, "cancel_check must be 0 or 1");
   if (o->cancel_check && o->accumulate) return fail(FEA_ERR_ARG, "cancel_check cannot be combined with accumulate");
+  if (m->mixed && (o->scatter == FEA_SCATTER_ROWOWNED || o->scatter == FEA_SCATTER_GATHER || o->cancel_check))
+    return fail(FEA_ERR_ARG, "a mesh of several element types scatters with atomics (no row-owned, gather or "
+                             "cancellation check)");
   return FEA_OK;
+}
+
+// The arguments restricted to one element block (the whole mesh for a single-type mesh).
+template <typename T>
+static void set_block(AsmArgs<T>& a, const fea_mesh::Block& b, const fea_pattern* p) {
+  a.conn = b.conn;
+  a.pos = p->pos + b.pos0;
+  a.n_elem = b.n_elem;
 }
 
 template <typename T>
@@ -423,11 +437,32 @@ struct Strategy {
   int groups;   // equation groups of the row-owned scatter
 };
 
-// FP32 element-parallel launch: the batched Hex8 kernel where the mesh has one, else the
-// per-type kernels behind launch_generic_f32.
-fea_status elem_f32(fea_mesh* m, const fea_pattern* p, const AsmArgs<float>& a, cudaStream_t s) {
-  if (m->type == FEA_HEX8 && p->plan) return plan_elem(p->plan, a, s);
-  return launch_generic_f32(a, m->type, s);
+// FP32 element-parallel launch over every element block: the batched Hex8 kernel where the
+// mesh has its schedule (single-type Hex8), else the per-type kernels behind launch_generic_f32.
+fea_status elem_f32(fea_mesh* m, const fea_pattern* p, const AsmArgs<float>& a0, cudaStream_t s) {
+  for (const fea_mesh::Block& b : m->blocks) {
+    if (b.n_elem == 0) continue;
+    AsmArgs<float> a = a0;
+    set_block(a, b, p);
+    if (b.type == FEA_HEX8 && p->plan) FEA_TRY(plan_elem(p->plan, a, s));
+    else FEA_TRY(launch_generic_f32(a, b.type, s));
+  }
+  return FEA_OK;
+}
+
+// The plain FP64 path over every element block: one launch per equation and block.
+fea_status elem_f64(fea_mesh* m, const fea_pattern* p, const AsmArgs<double>& a0, int32_t n_eq, cudaStream_t s) {
+  for (const fea_mesh::Block& b : m->blocks) {
+    if (b.n_elem == 0) continue;
+    AsmArgs<double> a = a0;
+    set_block(a, b, p);
+    for (int q = 0; q < n_eq; ++q) {  // geometry recomputed each time
+      a.eq0 = q;
+      a.eq_count = 1;
+      FEA_TRY(launch_generic_f64(a, b.type, s));
+    }
+  }
+  return FEA_OK;
 }
 
 bool stream_capturing(cudaStream_t s) {
@@ -472,11 +507,7 @@ fea_status run_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const void
   if (m->n_elem > 0) {
     if (!f32) {
       AsmArgs<double> a = make_args<double>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
-      for (int q = 0; q < n_eq; ++q) {  // one launch per equation, geometry recomputed each time
-        a.eq0 = q;
-        a.eq_count = 1;
-        FEA_TRY(launch_generic_f64(a, m->type, s));
-      }
+      FEA_TRY(elem_f64(m, p, a, n_eq, s));
     } else {
       AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
       if (rowowned) {
@@ -503,6 +534,11 @@ fea_status choose_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const v
   auto it = p->tuned.find(n_eq);
   if (it != p->tuned.end()) {
     *out = Strategy{it->second.first, it->second.second};
+    return FEA_OK;
+  }
+  if (m->mixed) {  // several element types: atomics only
+    p->tuned[n_eq] = std::make_pair((int)FEA_SCATTER_ATOMIC, 1);
+    *out = Strategy{FEA_SCATTER_ATOMIC, 1};
     return FEA_OK;
   }
   bool ro1 = false;
@@ -611,7 +647,31 @@ fea_status fea_pack_plan(const int64_t* count_by_type, int32_t n_types, int32_t 
 }
 
 }  // extern "C"
-static int nen_of(fea_elem_t t) { return t == FEA_TET4 ? 4 : t == FEA_HEX8 ? 8 : t == FEA_HEX27 ? 27 : 0; }
+static int nen_of(fea_elem_t t) {
+  return t == FEA_TET4 ? 4 : t == FEA_HEX8 ? 8 : t == FEA_HEX27 ? 27 : t == FEA_PEN6 ? 6 : t == FEA_PYR5 ? 5 : 0;
+}
+
+static void launch_validate(fea_elem_t type, const double* coords, const int32_t* conn, int64_t n_node,
+                            int64_t n_elem, uint32_t* status, cudaStream_t s) {
+  if (n_elem <= 0) return;
+  unsigned g = grid_for(n_elem, 128);
+  switch (type) {
+    case FEA_TET4: k_validate<FEA_TET4><<<g, 128, 0, s>>>(coords, conn, n_node, n_elem, status); break;
+    case FEA_HEX8: k_validate<FEA_HEX8><<<g, 128, 0, s>>>(coords, conn, n_node, n_elem, status); break;
+    case FEA_HEX27: k_validate<FEA_HEX27><<<g, 128, 0, s>>>(coords, conn, n_node, n_elem, status); break;
+    case FEA_PEN6: k_validate<FEA_PEN6><<<g, 128, 0, s>>>(coords, conn, n_node, n_elem, status); break;
+    case FEA_PYR5: k_validate<FEA_PYR5><<<g, 128, 0, s>>>(coords, conn, n_node, n_elem, status); break;
+  }
+}
+
+// Block b's connectivity rows [n][nen_b] into the padded array [n][nen_max] (-1 fills).
+__global__ void k_pad_conn(const int32_t* __restrict__ conn, int64_t n, int nen, int nen_max, int32_t* out) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nen_max) return;
+  int64_t e = t / nen_max;
+  int a = (int)(t - e * nen_max);
+  out[t] = a < nen ? conn[e * nen + a] : -1;
+}
 
 extern "C" {
 fea_status fea_mesh_destroy(fea_mesh* m) {
@@ -620,6 +680,7 @@ fea_status fea_mesh_destroy(fea_mesh* m) {
   cudaFree(m->xhi);
   cudaFree(m->xlo);
   cudaFree(m->conn);
+  cudaFree(m->conn_blocks);
   cudaFree(m->status);
   if (m->copy_ready) {
     for (int i = 0; i < fea_mesh::N_COPY; ++i) cudaStreamDestroy(m->copy_stream[i]);
@@ -680,14 +741,80 @@ fea_status fea_mesh_create(const double* coords, int64_t n_node, const int32_t* 
   }
   cudaMemsetAsync(m->status, 0, sizeof(uint32_t), s);
   k_split_coords<<<grid_for(n_node, 256), 256, 0, s>>>(m->coords, n_node, m->xhi, m->xlo);
-  if (n_elem > 0) {
-    unsigned g = grid_for(n_elem, 128);
-    if (type == FEA_TET4) k_validate<FEA_TET4><<<g, 128, 0, s>>>(m->coords, m->conn, n_node, n_elem, m->status);
-    else if (type == FEA_HEX8) k_validate<FEA_HEX8><<<g, 128, 0, s>>>(m->coords, m->conn, n_node, n_elem, m->status);
-    else k_validate<FEA_HEX27><<<g, 128, 0, s>>>(m->coords, m->conn, n_node, n_elem, m->status);
-  }
+  launch_validate(type, m->coords, m->conn, n_node, n_elem, m->status, s);
+  m->blocks.push_back(fea_mesh::Block{type, nen, 0, n_elem, m->conn, 0});
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cleanup(fail(FEA_ERR_CUDA, "validation launch: %s", cudaGetErrorString(e)));
+  fea_status st = fea_sync(m);
+  if (st != FEA_OK) return cleanup(st);
+  *out = m;
+  return FEA_OK;
+}
+
+fea_status fea_mesh_create_mixed(const double* coords, int64_t n_node, int32_t n_blocks, const fea_elem_t* types,
+                                 const int32_t* const* conns, const int64_t* n_elems, void* stream, fea_mesh** out) {
+  if (!out) return fail(FEA_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (n_blocks <= 0 || !types || !conns || !n_elems) return fail(FEA_ERR_ARG, "n_blocks must be > 0, arrays non-null");
+  if (n_blocks == 1) return fea_mesh_create(coords, n_node, conns[0], n_elems[0], types[0], stream, out);
+  if (n_node <= 0 || !coords) return fail(FEA_ERR_ARG, "n_node must be > 0 and coords non-null");
+  if (n_node >= INT32_MAX) return fail(FEA_ERR_TOO_LARGE, "n_node %lld exceeds int32 ids", (long long)n_node);
+  int nen_max = 0;
+  int64_t E = 0, conn_total = 0;
+  for (int b = 0; b < n_blocks; ++b) {
+    const int nen = nen_of(types[b]);
+    if (!nen) return fail(FEA_ERR_ARG, "block %d: unknown element type %d", b, (int)types[b]);
+    if (n_elems[b] < 0 || (n_elems[b] > 0 && !conns[b])) return fail(FEA_ERR_ARG, "block %d: bad size or null conn", b);
+    if (n_elems[b] > (int64_t)INT32_MAX / (nen * nen))
+      return fail(FEA_ERR_TOO_LARGE, "block %d: too many elements for int32 position-map indexing", b);
+    nen_max = std::max(nen_max, nen);
+    E += n_elems[b];
+    conn_total += n_elems[b] * nen;
+  }
+  if (E > (int64_t)INT32_MAX / nen_max) return fail(FEA_ERR_TOO_LARGE, "too many elements for int32 element ids");
+  fea_mesh* m = new (std::nothrow) fea_mesh();
+  if (!m) return fail(FEA_ERR_OOM, "host allocation failed");
+  m->type = types[0];
+  m->nen = nen_max;
+  m->n_node = n_node;
+  m->n_elem = E;
+  m->mixed = true;
+  m->stream = (cudaStream_t)stream;
+  cudaGetDevice(&m->device);
+  cudaStream_t s = m->stream;
+  auto cleanup = [&](fea_status st) { fea_mesh_destroy(m); return st; };
+  size_t cb = sizeof(double) * 3 * n_node;
+  if (cudaMalloc(&m->coords, cb) != cudaSuccess || cudaMalloc(&m->xhi, sizeof(float) * 3 * n_node) != cudaSuccess ||
+      cudaMalloc(&m->xlo, sizeof(float) * 3 * n_node) != cudaSuccess ||
+      cudaMalloc(&m->conn, sizeof(int32_t) * std::max<int64_t>(E * nen_max, 1)) != cudaSuccess ||
+      cudaMalloc(&m->conn_blocks, sizeof(int32_t) * std::max<int64_t>(conn_total, 1)) != cudaSuccess ||
+      cudaMalloc(&m->status, sizeof(uint32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(FEA_ERR_OOM, "device allocation of the mesh failed"));
+  }
+  cudaMemcpyKind kc = is_device_ptr(coords) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (cudaMemcpyAsync(m->coords, coords, cb, kc, s) != cudaSuccess) return cleanup(fail(FEA_ERR_CUDA, "coords copy failed"));
+  cudaMemsetAsync(m->status, 0, sizeof(uint32_t), s);
+  k_split_coords<<<grid_for(n_node, 256), 256, 0, s>>>(m->coords, n_node, m->xhi, m->xlo);
+  int64_t e0 = 0, c0 = 0, pos0 = 0;
+  for (int b = 0; b < n_blocks; ++b) {
+    const int nen = nen_of(types[b]);
+    const int64_t n = n_elems[b];
+    int32_t* cdst = m->conn_blocks + c0;
+    if (n > 0) {
+      cudaMemcpyKind ke = is_device_ptr(conns[b]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+      if (cudaMemcpyAsync(cdst, conns[b], sizeof(int32_t) * nen * n, ke, s) != cudaSuccess)
+        return cleanup(fail(FEA_ERR_CUDA, "block %d: conn copy failed", b));
+      k_pad_conn<<<grid_for(n * nen_max, 256), 256, 0, s>>>(cdst, n, nen, nen_max, m->conn + e0 * nen_max);
+      launch_validate(types[b], m->coords, cdst, n_node, n, m->status, s);
+    }
+    m->blocks.push_back(fea_mesh::Block{types[b], nen, e0, n, cdst, pos0});
+    e0 += n;
+    c0 += n * nen;
+    pos0 += n * nen * nen;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cleanup(fail(FEA_ERR_CUDA, "mesh setup launch: %s", cudaGetErrorString(e)));
   fea_status st = fea_sync(m);
   if (st != FEA_OK) return cleanup(st);
   *out = m;
@@ -718,6 +845,12 @@ fea_status fea_pattern_get(const fea_pattern* p, const int64_t** rowptr, const i
   if (pos) *pos = p->pos;
   if (nnz) *nnz = p->nnz;
   return FEA_OK;
+}
+
+static int64_t pos_total(const fea_mesh* m) {
+  int64_t t = 0;
+  for (const fea_mesh::Block& b : m->blocks) t += b.n_elem * b.nen * b.nen;
+  return t;
 }
 
 fea_status fea_pattern_build(fea_mesh* m, fea_pattern** out) {
@@ -772,13 +905,16 @@ fea_status fea_pattern_build(fea_mesh* m, fea_pattern** out) {
   p->nnz = nnz;
   p->maxcol = maxcol;
   if (cudaMalloc(&p->colind, sizeof(int32_t) * std::max<int64_t>(nnz, 1)) != cudaSuccess ||
-      cudaMalloc(&p->pos, sizeof(int32_t) * std::max<int64_t>(tot * nen, 1)) != cudaSuccess) {
+      cudaMalloc(&p->pos, sizeof(int32_t) * std::max<int64_t>(pos_total(m), 1)) != cudaSuccess) {
     cudaGetLastError();
     return done(fail(FEA_ERR_OOM, "device allocation of colind/pos failed"));
   }
   k_rows<<<rg, ROW_WARPS * 32, smem, s>>>(m->conn, nen, p->inc_ptr, p->inc_elem, N, 1, nullptr, p->rowptr, p->colind,
                                           m->status);
-  if (tot > 0) k_posmap<<<grid_for(tot * nen, 256), 256, 0, s>>>(m->conn, E, nen, p->rowptr, p->colind, p->pos);
+  for (const fea_mesh::Block& b : m->blocks)  // each block's own [n][nen_b][nen_b] map
+    if (b.n_elem > 0)
+      k_posmap<<<grid_for(b.n_elem * b.nen * b.nen, 256), 256, 0, s>>>(b.conn, b.n_elem, b.nen, p->rowptr,
+                                                                        p->colind, p->pos + b.pos0);
   if (cudaMalloc(&p->inc_local, std::max<int64_t>(tot, 1)) != cudaSuccess) {
     cudaGetLastError();
     return done(fail(FEA_ERR_OOM, "device allocation of the incidence index failed"));
@@ -845,11 +981,7 @@ fea_status fea_residual(fea_mesh* m, const fea_pattern* p, const void* vel, cons
       AsmArgs<double> a = make_args<double>(m, p, vel, kd, sr, phi_old, dt, n_eq, &o, nullptr, nullptr);
       a.phi_eval = (const double*)phi;
       a.resid = (double*)r;
-      for (int q = 0; q < n_eq; ++q) {
-        a.eq0 = q;
-        a.eq_count = 1;
-        FEA_TRY(launch_generic_f64(a, m->type, s));
-      }
+      FEA_TRY(elem_f64(m, p, a, n_eq, s));
     } else {
       AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi_old, dt, n_eq, &o, nullptr, nullptr);
       a.phi_eval = (const float*)phi;

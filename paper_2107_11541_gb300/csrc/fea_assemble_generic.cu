@@ -93,6 +93,8 @@ static fea_status launch_any(const AsmArgs<T>& a, fea_elem_t type, cudaStream_t 
     case FEA_TET4: return launch_t<T, FEA_TET4>(a, s);
     case FEA_HEX8: return launch_t<T, FEA_HEX8>(a, s);
     case FEA_HEX27: return launch_t<T, FEA_HEX27>(a, s);
+    case FEA_PEN6: return launch_t<T, FEA_PEN6>(a, s);
+    case FEA_PYR5: return launch_t<T, FEA_PYR5>(a, s);
   }
   return fail(FEA_ERR_ARG, "unknown element type");
 }

@@ -149,6 +149,8 @@ fea_status launch_rows_any(const RowArgs& r, fea_elem_t type, cudaStream_t s) {
     case FEA_TET4: return launch_rows<TC, FEA_TET4, MODE>(r, s);
     case FEA_HEX8: return launch_rows<TC, FEA_HEX8, MODE>(r, s);
     case FEA_HEX27: return launch_rows<TC, FEA_HEX27, MODE>(r, s);
+    case FEA_PEN6: return launch_rows<TC, FEA_PEN6, MODE>(r, s);
+    case FEA_PYR5: return launch_rows<TC, FEA_PYR5, MODE>(r, s);
   }
   return fail(FEA_ERR_ARG, "unknown element type");
 }

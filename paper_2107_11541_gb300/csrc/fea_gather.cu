@@ -183,6 +183,8 @@ fea_status launch_gather_f32(const AsmArgs<float>& a, fea_elem_t type, int maxco
     case FEA_TET4: return launch_t<4>(g, maxcol, s);
     case FEA_HEX8: return launch_t<8>(g, maxcol, s);
     case FEA_HEX27: return launch_t<27>(g, maxcol, s);
+    case FEA_PEN6: return launch_t<6>(g, maxcol, s);
+    case FEA_PYR5: return launch_t<5>(g, maxcol, s);
   }
   return fail(FEA_ERR_ARG, "unknown element type");
 }

@@ -65,8 +65,19 @@ struct fea_mesh {
   double* coords;     // [n_node][3] FP64
   float* xhi;         // [3][n_node] high part of each coordinate (float)
   float* xlo;         // [3][n_node] low part: coordinate - hi, rounded to float
-  int32_t* conn;      // [n_elem][nen]
+  int32_t* conn;      // [n_elem][nen]; several types: padded with -1 to the largest nen (pattern build)
   uint32_t* status;   // device status word
+  // element blocks, one per type (a single-type mesh has one block whose conn is conn)
+  struct Block {
+    fea_elem_t type;
+    int nen;
+    int64_t e0, n_elem;  // first element (numbered block by block) and count
+    int32_t* conn;       // [n_elem][nen], device
+    int64_t pos0;        // offset of the block's [n_elem][nen][nen] position map
+  };
+  std::vector<Block> blocks;
+  bool mixed;            // more than one block
+  int32_t* conn_blocks;  // several types: the blocks' own connectivity, concatenated
   // fea_assemble_host: side streams and events for concurrent host<->device copies
   static constexpr int N_COPY = 4;
   cudaStream_t copy_stream[N_COPY];
@@ -111,11 +122,20 @@ namespace fea {
 // Hex27: triquadratic, node a = i+3j+9k <-> {-1,0,1}^3;
 //   3x3x3 Gauss-Legendre, points 0, +-sqrt(3/5), weights 8/9, 5/9.
 // Gauss points are numbered like the nodes (x fastest).
+// Pen6:  prism, linear triangle (1-xi-eta, xi, eta) times linear (1-+zeta)/2; node i + 3k is
+//   triangle vertex i ((0,0), (1,0), (0,1)) on zeta = -1 (k = 0) or +1 (k = 1); triangle
+//   points (1/6,1/6), (2/3,1/6), (1/6,2/3) (weight 1/6) times Gauss +-1/sqrt3, point t + 3k.
+// Pyr5:  pyramid |xi|,|eta| <= 1-zeta, 0 <= zeta <= 1; base corners (-1,-1), (1,-1), (1,1),
+//   (-1,1) with N_a = [(1-zeta) + xa xi + ya eta + xa ya xi eta/(1-zeta)]/4, apex N_4 = zeta;
+//   points of a collapsed cube: xi = r (1-zeta), eta = s (1-zeta), r, s = +-1/sqrt3, zeta the
+//   3 Gauss points mapped to [0,1], weight w_zeta/2 (1-zeta)^2; point i + 2j + 4k.
 
 template <int TYPE> struct Elem;
 template <> struct Elem<FEA_TET4> { static constexpr int NEN = 4, NG = 4, ORDER = 1; };
 template <> struct Elem<FEA_HEX8> { static constexpr int NEN = 8, NG = 8, ORDER = 1; };
 template <> struct Elem<FEA_HEX27> { static constexpr int NEN = 27, NG = 27, ORDER = 2; };
+template <> struct Elem<FEA_PEN6> { static constexpr int NEN = 6, NG = 6, ORDER = 1; };
+template <> struct Elem<FEA_PYR5> { static constexpr int NEN = 5, NG = 12, ORDER = 1; };
 
 // 1-D Lagrange basis on [-1,1]: value and derivative of function i at t.
 template <int ORDER, typename T>
@@ -146,6 +166,21 @@ __host__ __device__ inline void gauss_point(int g, double xi[3], double& w) {
     xi[1] = (g & 2) ? p : -p;
     xi[2] = (g & 4) ? p : -p;
     w = 1.0;
+  } else if (TYPE == FEA_PEN6) {
+    const int t = g % 3;
+    xi[0] = t == 1 ? 2.0 / 3.0 : 1.0 / 6.0;
+    xi[1] = t == 2 ? 2.0 / 3.0 : 1.0 / 6.0;
+    xi[2] = g < 3 ? -0.57735026918962576451 : 0.57735026918962576451;
+    w = 1.0 / 6.0;
+  } else if (TYPE == FEA_PYR5) {
+    const double p = 0.57735026918962576451, q = 0.77459666924148337704;  // 1/sqrt3, sqrt(3/5)
+    const int k = g >> 2;
+    const double t = k == 0 ? -q : (k == 1 ? 0.0 : q), wz = k == 1 ? 8.0 / 9.0 : 5.0 / 9.0;
+    const double z = 0.5 * (1.0 + t), c = 1.0 - z;
+    xi[0] = ((g & 1) ? p : -p) * c;
+    xi[1] = ((g & 2) ? p : -p) * c;
+    xi[2] = z;
+    w = 0.5 * wz * c * c;
   } else {
     const double p = 0.77459666924148337704;  // sqrt(3/5)
     const double pt[3] = {-p, 0.0, p};
@@ -164,6 +199,28 @@ __host__ __device__ inline void shape(int a, const T xi[3], T& N, T dN[3]) {
   if (TYPE == FEA_TET4) {
     if (a == 0) { N = T(1) - xi[0] - xi[1] - xi[2]; dN[0] = dN[1] = dN[2] = T(-1); }
     else { N = xi[a - 1]; dN[0] = a == 1; dN[1] = a == 2; dN[2] = a == 3; }
+  } else if (TYPE == FEA_PEN6) {
+    const int i = a % 3;
+    const T l = a < 3 ? T(0.5) * (T(1) - xi[2]) : T(0.5) * (T(1) + xi[2]), dl = a < 3 ? T(-0.5) : T(0.5);
+    const T L = i == 0 ? T(1) - xi[0] - xi[1] : xi[i - 1];
+    const T dLx = i == 0 ? T(-1) : (i == 1 ? T(1) : T(0)), dLy = i == 0 ? T(-1) : (i == 2 ? T(1) : T(0));
+    N = L * l;
+    dN[0] = dLx * l;
+    dN[1] = dLy * l;
+    dN[2] = L * dl;
+  } else if (TYPE == FEA_PYR5) {
+    if (a == 4) {
+      N = xi[2];
+      dN[0] = dN[1] = T(0);
+      dN[2] = T(1);
+    } else {
+      const T sx = (a == 1 || a == 2) ? T(1) : T(-1), sy = a >= 2 ? T(1) : T(-1), c = T(1) - xi[2];
+      const T sxy = sx * sy;
+      N = T(0.25) * (c + sx * xi[0] + sy * xi[1] + sxy * xi[0] * xi[1] / c);
+      dN[0] = T(0.25) * (sx + sxy * xi[1] / c);
+      dN[1] = T(0.25) * (sy + sxy * xi[0] / c);
+      dN[2] = T(0.25) * (T(-1) + sxy * xi[0] * xi[1] / (c * c));
+    }
   } else {
     constexpr int ORDER = Elem<TYPE>::ORDER, Q = ORDER + 1;
     int i = a % Q, j = (a / Q) % Q, k = a / (Q * Q);
@@ -178,18 +235,25 @@ __host__ __device__ inline void shape(int a, const T xi[3], T& N, T dN[3]) {
   }
 }
 
-// Corner points used by the orientation check (Tet4 vertices, hex corners).
+// Corner points used by the orientation check (Tet4 and Pen6 vertices, hex corners, the
+// pyramid's base corners: its rational functions are singular at the apex).
 template <int TYPE>
 __host__ __device__ inline void corner_point(int c, double xi[3]) {
   if (TYPE == FEA_TET4) {
     xi[0] = c == 1; xi[1] = c == 2; xi[2] = c == 3;
+  } else if (TYPE == FEA_PEN6) {
+    xi[0] = c % 3 == 1; xi[1] = c % 3 == 2; xi[2] = c < 3 ? -1.0 : 1.0;
+  } else if (TYPE == FEA_PYR5) {
+    xi[0] = (c == 1 || c == 2) ? 1.0 : -1.0; xi[1] = c >= 2 ? 1.0 : -1.0; xi[2] = 0.0;
   } else {
     xi[0] = (c & 1) ? 1.0 : -1.0;
     xi[1] = (c & 2) ? 1.0 : -1.0;
     xi[2] = (c & 4) ? 1.0 : -1.0;
   }
 }
-template <int TYPE> constexpr int n_corners() { return TYPE == FEA_TET4 ? 4 : 8; }
+template <int TYPE> constexpr int n_corners() {
+  return TYPE == FEA_TET4 ? 4 : TYPE == FEA_PEN6 ? 6 : TYPE == FEA_PYR5 ? 4 : 8;
+}
 
 template <typename T>
 __host__ __device__ inline T det3(const T J[3][3]) {

@@ -427,7 +427,7 @@ static fea_status build_variant(fea_rowowned_plan* P, int n_eq, Variant* v) {
 
 fea_status plan_build(fea_mesh* m, fea_pattern* p, fea_rowowned_plan** out) {
   *out = nullptr;
-  if (m->type != FEA_HEX8 || m->n_elem == 0) return FEA_OK;
+  if (m->mixed || m->type != FEA_HEX8 || m->n_elem == 0) return FEA_OK;
   fea_rowowned_plan* P = new (std::nothrow) fea_rowowned_plan();
   if (!P) return fail(FEA_ERR_OOM, "host allocation failed");
   P->mesh = m;

@@ -15,16 +15,16 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libfea.so")
 
-FEA_TET4, FEA_HEX8, FEA_HEX27 = 0, 1, 2
+FEA_TET4, FEA_HEX8, FEA_HEX27, FEA_PEN6, FEA_PYR5 = 0, 1, 2, 3, 4
 FEA_F64_PLAIN, FEA_F32_FUSED = 0, 1
 FEA_TERM_MASS, FEA_TERM_CONV, FEA_TERM_DIFF, FEA_TERM_REAC, FEA_TERM_SUPG, FEA_TERM_ALL = 1, 2, 4, 8, 16, 31
 FEA_SCATTER_AUTO, FEA_SCATTER_ATOMIC, FEA_SCATTER_ROWOWNED, FEA_SCATTER_GATHER = 0, 1, 2, 3
 STATUS = {0: "FEA_OK", 1: "FEA_ERR_ARG", 2: "FEA_ERR_RANGE", 3: "FEA_ERR_DUP_NODE", 4: "FEA_ERR_INVERTED",
           5: "FEA_ERR_TOO_LARGE", 6: "FEA_ERR_OOM", 7: "FEA_ERR_CUDA", 8: "FEA_ERR_TIMEOUT", 9: "FEA_ERR_STATE"}
-NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27}
+NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27, FEA_PEN6: 6, FEA_PYR5: 5}
 
 # Every symbol include/fea.h declares (checked by the tests).
-EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_destroy", "fea_mesh_set_stream", "fea_sync",
+EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_create_mixed", "fea_mesh_destroy", "fea_mesh_set_stream", "fea_sync",
            "fea_pattern_build", "fea_pattern_get", "fea_pattern_destroy", "fea_assemble", "fea_residual",
            "fea_assemble_host",
            "fea_pack_plan", "fea_csr_rowptr_noalloc", "fea_update_fields", "fea_graph_capture_steps",
@@ -59,6 +59,7 @@ def lib(path: str = LIB_PATH):
         vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int32, C.c_double
         L.fea_default_opts.argtypes = [C.POINTER(fea_assemble_opts)]
         L.fea_mesh_create.argtypes = [vp, i64, vp, i64, C.c_int, vp, C.POINTER(vp)]
+        L.fea_mesh_create_mixed.argtypes = [vp, i64, i32, vp, vp, vp, vp, C.POINTER(vp)]
         L.fea_mesh_destroy.argtypes = [vp]
         L.fea_mesh_set_stream.argtypes = [vp, vp]
         L.fea_sync.argtypes = [vp]
@@ -129,6 +130,22 @@ def fea_mesh_create(coords, conn, elem_type: int, stream=None) -> C.c_void_p:
     out = C.c_void_p()
     _check(lib().fea_mesh_create(_ptr(coords), coords.shape[0], _ptr(conn), conn.shape[0], int(elem_type),
                                  _stream_ptr(stream), C.byref(out)))
+    return out
+
+
+def fea_mesh_create_mixed(coords, blocks, stream=None) -> C.c_void_p:
+    """coords [N][3] float64 and blocks [(elem_type, conn [E_b][nen_b] int32), ...] (numpy or
+    torch CUDA tensors); elements are numbered block by block."""
+    if isinstance(coords, np.ndarray):
+        coords = np.ascontiguousarray(coords, dtype=np.float64)
+    conns = [np.ascontiguousarray(c, dtype=np.int32) if isinstance(c, np.ndarray) else c for _, c in blocks]
+    nb = len(blocks)
+    types = (C.c_int * nb)(*[int(t) for t, _ in blocks])
+    ptrs = (C.c_void_p * nb)(*[_ptr(c) for c in conns])
+    counts = (C.c_int64 * nb)(*[int(c.shape[0]) for c in conns])
+    out = C.c_void_p()
+    _check(lib().fea_mesh_create_mixed(_ptr(coords), coords.shape[0], nb, types, ptrs, counts, _stream_ptr(stream),
+                                       C.byref(out)))
     return out
 
 
