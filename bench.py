@@ -29,6 +29,9 @@ sys.path.insert(0, ROOT)
 from paper_2107_11541_gb300 import meshgen as G  # noqa: E402
 
 WORKLOADS = {"tet4_100_perm_1eq": 1, "hex8_128_21eq": 2, "hex27_48_11eq": 3, "hex8_256_32eq": 4}
+# meshes of several element types (not among the paper-shaped configurations): cells per axis, equations
+MIXED_WORKLOADS = {"mixed_96_4eq": (96, 4)}
+NG = {G.TET4: 4, G.HEX8: 8, G.HEX27: 27, G.PEN6: 6, G.PYR5: 12}
 DEFAULT_WORKLOAD = "hex8_128_21eq"
 METRIC = "elements x equations assembled per second (FP32 batched)"
 UNIT = "elem*eq/s"
@@ -44,11 +47,11 @@ def algorithmic_bytes(E, N, nnz, nen, q, s=4):
     return 4 * E * nen + 6 * N * s + 3 * q * N * s + q * (nnz + N) * s
 
 
-def algorithmic_flops_per_elem_eq(nen):
+def algorithmic_flops_per_elem_eq(nen, ng=None):
     """Multiply-adds of the operator in its direct form, per element and equation: the rank-NG
     Galerkin/SUPG product (NG NEN^2), the symmetric diffusion sum (NG NEN(NEN+1)/2) and the
-    interpolation/test-function/RHS vectors (6 NG NEN); NG = NEN for all three element types."""
-    ng = nen
+    interpolation/test-function/RHS vectors (6 NG NEN); NG = NEN except for the pyramid (12)."""
+    ng = nen if ng is None else ng
     return 2 * (ng * nen * nen + ng * nen * (nen + 1) // 2 + 6 * ng * nen)
 
 
@@ -286,7 +289,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(MIXED_WORKLOADS))
     ap.add_argument("--scatter", type=int, default=0, help="0 auto, 1 atomic, 2 row-owned, 3 gather")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -305,6 +308,9 @@ def main():
     if args.graph is None:
         args.graph = 1 if args.workload == "hex8_256_32eq" else 0
     rank, world, local = dist_env()
+    if args.workload in MIXED_WORKLOADS:
+        run_mixed(args, rank, world, local)
+        return
     w = make(args.workload, args.cells)
     if args.impl == "reference":
         run_reference(args, w, rank)
@@ -503,6 +509,162 @@ def main():
                                "sample": f"elements [0, {ne_all}) of {m.n_elem} in {procs} contiguous chunks, one "
                                          f"process per host core, all {qq} equations, FP64 C oracle"}
         out["cpu_baseline_single"] = single
+    fea.fea_pattern_destroy(p)
+    fea.fea_mesh_destroy(h)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def make_mixed(workload: str, n=None):
+    """The Hex8 / Pyr5 / Pen6 layered unit cube (interior nodes moved by up to 0.1 h) and its
+    fields, seeded like the other workloads."""
+    cells, q = MIXED_WORKLOADS[workload]
+    mm = G.mixed_mesh(n or cells)
+    rng = np.random.default_rng(G.SEED_BASE + 100)
+    G.perturb_interior(mm, rng, 0.1)
+    return mm, G.draw_fields(rng, mm.coords, q, 50.0)
+
+
+def mixed_parity(mm, fields, values, rhs, rowptr, colind, n_rows=48, seed=5):
+    """Sampled rows of a mesh of several element types against the oracle: the elements incident
+    to the sampled nodes, of every block, assembled by the oracle give those rows complete."""
+    import oracle as O
+    rng = np.random.default_rng(seed)
+    rows = np.unique(np.concatenate([[0, mm.n_node - 1], rng.integers(0, mm.n_node, n_rows)]))
+    sub = [(t, c[np.isin(c, rows).any(axis=1)]) for t, c in mm.blocks]
+    sub = [(t, c) for t, c in sub if c.shape[0] > 0]
+    srp, sci, _ = O.pattern_mixed(sub, mm.n_node, with_pos=False)
+    wide = fields.astype(np.float32).astype(np.float64)
+    ref, refb, _, absb = O.assemble_mixed(mm.coords, sub, srp, sci, wide, with_abs=True)
+    worst_a = worst_b = 0.0
+    for r in rows:
+        k0, k1, s0, s1 = rowptr[r], rowptr[r + 1], srp[r], srp[r + 1]
+        assert np.array_equal(colind[k0:k1], sci[s0:s1])
+        got = values[:, k0:k1].astype(np.float64)
+        want = ref[:, s0:s1]
+        den = np.sqrt((want ** 2).sum(axis=1))
+        worst_a = max(worst_a, float((np.sqrt(((got - want) ** 2).sum(axis=1)) / np.where(den > 0, den, 1)).max()))
+        eb = np.abs(rhs[:, r].astype(np.float64) - refb[:, r]) / np.where(absb[:, r] > 0, absb[:, r], 1.0)
+        worst_b = max(worst_b, float(eb.max()))
+    return {"rows": int(rows.size), "max_row_err_A": worst_a, "max_err_b": worst_b, "tol": 1e-5,
+            "pass": worst_a <= 1e-5 and worst_b <= 1e-5}
+
+
+def run_mixed(args, rank, world, local):
+    """A mesh of Hex8, Pyr5 and Pen6 blocks: the same measurement as the single-type workloads
+    (device-resident step, end to end, FP64 plain, sampled parity, oracle on the host)."""
+    mm, fld = make_mixed(args.workload, args.cells)
+    q = fld.n_eq
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "the reference arm times the paper-shaped "
+                              "configurations; this workload has no oracle-on-all-cores line"}), flush=True)
+        return
+    import torch
+    from paper_2107_11541_gb300 import fea
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    stream = torch.cuda.Stream()
+    h = fea.fea_mesh_create_mixed(mm.coords, mm.blocks, stream)
+    p = fea.fea_pattern_build(h)
+    r_, c_, _, nnz = fea.fea_pattern_get(p)
+    f32 = fld.astype(np.float32)
+    with torch.cuda.stream(stream):
+        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (f32.velocity, f32.diffusivity,
+                                                                          f32.reaction, f32.phi_old)]
+        values = torch.empty((q, nnz), dtype=torch.float32, device="cuda")
+        rhs = torch.empty((q, mm.n_node), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    opts = fea.fea_default_opts()
+    for _ in range(args.warmup):
+        fea.fea_assemble(h, p, *dev, fld.dt, q, opts, values, rhs)
+    fea.fea_sync(h)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for a, b in kev:
+        a.record(stream)
+        b.record(stream)
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = fea.fea_kernel_launches()
+    clocks.start()
+    time.sleep(0.3)
+    t0e.record(stream)
+    for a, b in kev:
+        opts.event_begin, opts.event_end = a.cuda_event, b.cuda_event
+        fea.fea_assemble(h, p, *dev, fld.dt, q, opts, values, rhs)
+    t1e.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = fea.fea_kernel_launches() - launches0
+    fea.fea_sync(h)
+    opts.event_begin = opts.event_end = None
+    ms = t0e.elapsed_time(t1e) / args.steps
+    kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
+    ms, kernel_ms, value = aggregate_over_ranks(ms, kernel_ms, mm.n_elem * q, world, dist, "cuda")
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else HBM_PEAK_FALLBACK
+    abytes = sum(4 * c.size for _, c in mm.blocks) + 6 * mm.n_node * 4 + 3 * q * mm.n_node * 4 + \
+        q * (nnz + mm.n_node) * 4
+    aflops = sum(algorithmic_flops_per_elem_eq(G.NEN[t], NG[t]) * c.shape[0] for t, c in mm.blocks) * q
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    hbm_ach, alu_ach = abytes / (kernel_ms * 1e-3) / 1e9, aflops / (kernel_ms * 1e-3) / 1e12
+    hbm_obj = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
+               "traffic": None, "algorithmic_bytes": abytes, "peak_source": "measured" if peaks else "fallback"}
+    alu_obj = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+               "traffic": None, "algorithmic_flops": aflops,
+               "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    t_hbm, t_alu = abytes / (hbm_peak * 1e9), aflops / (alu_peak * 1e12)
+    roof, other = (alu_obj, hbm_obj) if t_alu > t_hbm else (hbm_obj, alu_obj)
+    config = {"workload": args.workload, "elem_types": {G.NAMES[t]: int(c.shape[0]) for t, c in mm.blocks},
+              "elements": mm.n_elem, "nodes": mm.n_node, "nnz": int(nnz), "n_eq": q, "precision": "f32_fused",
+              "l2": "no flush: inputs + outputs per step exceed the 129 MB L2", "scatter": "atomic"}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config, "clocks": clk,
+           "gpu_launches": int(launches), "kernel_ms": kernel_ms, "roofline": roof, "roofline_other": other}
+    if rank == 0 and not args.no_parity:
+        rowptr = torch.as_tensor(fea._DevView(r_, (mm.n_node + 1,), "<i8"), device="cuda").cpu().numpy()
+        colind = torch.as_tensor(fea._DevView(c_, (nnz,), "<i4"), device="cuda").cpu().numpy()
+        out["parity"] = mixed_parity(mm, fld, values.cpu().numpy(), rhs.cpu().numpy(), rowptr, colind)
+    if not args.no_f64:
+        d64 = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (fld.velocity, fld.diffusivity,
+                                                                          fld.reaction, fld.phi_old)]
+        v64 = torch.empty((q, nnz), dtype=torch.float64, device="cuda")
+        r64 = torch.empty((q, mm.n_node), dtype=torch.float64, device="cuda")
+        o64 = fea.fea_default_opts(precision=fea.FEA_F64_PLAIN)
+        fea.fea_assemble(h, p, *d64, fld.dt, q, o64, v64, r64)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fea.fea_assemble(h, p, *d64, fld.dt, q, o64, v64, r64)
+        b.record(stream)
+        torch.cuda.synchronize()
+        t64 = a.elapsed_time(b)
+        v_f64 = mm.n_elem * q / (t64 * 1e-3)
+        out["fp64_plain"] = {"value": v_f64, "unit": UNIT, "ms_per_step": t64, "equations_timed": q,
+                             "speedup_f32_fused": value / world / v_f64}
+        del d64, v64, r64
+    if not args.no_e2e:
+        out["e2e"] = end_to_end(h, p, f32, mm, nnz, q, stream, min(args.steps, 5), world, dist)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        import oracle as O
+        sub = [(t, c[: max(1, c.shape[0] // 64)]) for t, c in mm.blocks]
+        srp, sci, _ = O.pattern_mixed(sub, mm.n_node, with_pos=False)
+        wide = fld.astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        O.assemble_mixed(mm.coords, sub, srp, sci, wide)
+        dt_cpu = time.perf_counter() - t0
+        ne = sum(c.shape[0] for _, c in sub)
+        out["cpu_baseline"] = {"value": ne * q / dt_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"the first 1/64 of every block ({ne} of {mm.n_elem} elements), all {q} "
+                                         f"equations, FP64 C oracle, single thread"}
     fea.fea_pattern_destroy(p)
     fea.fea_mesh_destroy(h)
     if rank == 0:
