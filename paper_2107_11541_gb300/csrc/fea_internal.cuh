@@ -330,6 +330,8 @@ fea_status launch_generic_f64(const AsmArgs<double>& a, fea_elem_t type, cudaStr
 fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s);
 // FP32 Tet4: one thread per (element, equation) (atomics, or the gather scratch if a.em).
 fea_status launch_tet4_f32(const AsmArgs<float>& a, cudaStream_t s);
+// FP32 Pen6 / Pyr5: one thread per (element, equation) item, per-point geometry in registers.
+fea_status launch_small_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s);
 // FP32 Hex27, one CTA per element, full operator and up to 12 equations (hex27_kernel_applies).
 bool hex27_kernel_applies(const AsmArgs<float>& a);
 fea_status launch_hex27_f32(const AsmArgs<float>& a, cudaStream_t s);

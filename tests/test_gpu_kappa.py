@@ -15,36 +15,63 @@ from paper_2107_11541_gb300 import meshgen as G
 pytestmark = pytest.mark.gpu
 
 
-def rotated_slab(cfg, n, q):
-    w = G.make_workload(cfg, n=n, n_eq=q, stretched_slab=True)
+def rotation():
     a, b, c = 0.3, 0.5, 0.7
     rx = np.array([[1, 0, 0], [0, np.cos(a), -np.sin(a)], [0, np.sin(a), np.cos(a)]])
     ry = np.array([[np.cos(b), 0, np.sin(b)], [0, 1, 0], [-np.sin(b), 0, np.cos(b)]])
     rz = np.array([[np.cos(c), -np.sin(c), 0], [np.sin(c), np.cos(c), 0], [0, 0, 1]])
-    w.mesh.coords = w.mesh.coords @ (rz @ ry @ rx).T
-    return w
+    return rz @ ry @ rx
 
 
-@pytest.mark.parametrize("cfg,n,q,scatter", [(2, 6, 2, fea.FEA_SCATTER_ROWOWNED), (2, 6, 2, fea.FEA_SCATTER_GATHER),
-                                             (3, 3, 2, fea.FEA_SCATTER_ATOMIC), (3, 3, 2, fea.FEA_SCATTER_GATHER)],
-                         ids=["hex8_rowowned", "hex8_gather", "hex27_atomic", "hex27_gather"])
-def test_kappa_fallback_keeps_fp32_parity(cfg, n, q, scatter):
+def rotated_slab(cfg, n, q):
+    w = G.make_workload(cfg, n=n, n_eq=q, stretched_slab=True)
+    w.mesh.coords = w.mesh.coords @ rotation().T
+    return w.mesh, w.fields
+
+
+def rotated_prism_slab(n, q):
+    """Prisms (triangles in the y-z planes) with the middle z layer 1e-4 as thick as the others."""
+    widths = np.ones(n)
+    widths[n // 2] = 1e-4
+    widths /= widths.sum()
+    faces = np.concatenate([[0.0], np.cumsum(widths)])
+    faces[-1] = 1.0
+    mesh = G.structured_mesh(G.PEN6, n, faces)
+    fields = G.draw_fields(np.random.default_rng(12), mesh.coords, q, 50.0)
+    mesh.coords = mesh.coords @ rotation().T
+    return mesh, fields
+
+
+def check_fallback(mesh, fields, q, scatter):
     import torch
-    w = rotated_slab(cfg, n, q)
-    run = GpuRun(w.mesh)
+    run = GpuRun(mesh)
     try:
         errs = {}
         for kappa in (1e3, 1e30):
-            (vel, kd, sr, phi), _ = run.upload(w.fields, fea.FEA_F32_FUSED)
+            (vel, kd, sr, phi), _ = run.upload(fields, fea.FEA_F32_FUSED)
             vals = torch.empty((q, run.nnz), device="cuda")
-            rhs = torch.empty((q, w.mesh.n_node), device="cuda")
+            rhs = torch.empty((q, mesh.n_node), device="cuda")
             opts = fea.fea_default_opts(scatter=scatter, kappa_threshold=kappa)
-            fea.fea_assemble(run.handle, run.pattern, vel, kd, sr, phi, w.fields.dt, q, opts, vals, rhs)
+            fea.fea_assemble(run.handle, run.pattern, vel, kd, sr, phi, fields.dt, q, opts, vals, rhs)
             fea.fea_sync(run.handle)
-            errs[kappa] = compare_full(run, w.fields, fea.FEA_F32_FUSED, values=vals, rhs=rhs)
+            errs[kappa] = compare_full(run, fields, fea.FEA_F32_FUSED, values=vals, rhs=rhs)
         ea, eb = errs[1e3]
         assert ea <= TOL_F32 and eb <= TOL_F32, errs
         # without the fallback the thin elements' FP32 inverse is visibly worse
         assert errs[1e30][0] > ea, errs
     finally:
         run.close()
+
+
+@pytest.mark.parametrize("cfg,n,q,scatter", [(2, 6, 2, fea.FEA_SCATTER_ROWOWNED), (2, 6, 2, fea.FEA_SCATTER_GATHER),
+                                             (3, 3, 2, fea.FEA_SCATTER_ATOMIC), (3, 3, 2, fea.FEA_SCATTER_GATHER)],
+                         ids=["hex8_rowowned", "hex8_gather", "hex27_atomic", "hex27_gather"])
+def test_kappa_fallback_keeps_fp32_parity(cfg, n, q, scatter):
+    mesh, fields = rotated_slab(cfg, n, q)
+    check_fallback(mesh, fields, q, scatter)
+
+
+@pytest.mark.parametrize("scatter", [fea.FEA_SCATTER_ATOMIC, fea.FEA_SCATTER_GATHER], ids=["atomic", "gather"])
+def test_kappa_fallback_prisms(scatter):
+    mesh, fields = rotated_prism_slab(5, 2)
+    check_fallback(mesh, fields, 2, scatter)
