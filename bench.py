@@ -301,6 +301,8 @@ def main():
                     help="also time the matrix-free residual r = b - A phi (fea_residual) on the same workload")
     ap.add_argument("--spmv", action="store_true",
                     help="also time the batched SpMV y_q = A_q x_q (fea_spmv) on the assembled matrices")
+    ap.add_argument("--pcg", action="store_true",
+                    help="also time the batched Jacobi-preconditioned CG (fea_pcg) on the MASS + DIFF matrices")
     ap.add_argument("--graph", type=int, default=None,
                     help="1: time the K steps as one CUDA graph of K (assemble, field update) time steps "
                          "(default on for hex8_256_32eq)")
@@ -460,6 +462,29 @@ def main():
         out["spmv"] = {"ms": sms, "algorithmic_bytes": sbytes, "achieved_gbs": sbytes / (sms * 1e-3) / 1e9,
                        "frac_of_hbm": sbytes / (sms * 1e-3) / 1e9 / hbm_peak}
         del xs, ys
+    if args.pcg:
+        # symmetric positive definite systems of the same mesh: mass + diffusion; 10 iterations with rtol 0 keep
+        # every equation iterating (many more drive the mass-dominated FP32 residual to exactly 0, which stops it)
+        po = fea.fea_default_opts(terms=fea.FEA_TERM_MASS | fea.FEA_TERM_DIFF, scatter=args.scatter)
+        fea.fea_assemble(h, p, *dev, fld.dt, q, po, values, rhs)
+        fea.fea_sync(h)
+        xs = torch.zeros((q, m.n_node), dtype=torch.float32, device="cuda")
+        fea.fea_pcg(p, values, rhs, xs, q, 3, 0.0, stream)  # workspace and diagonal positions
+        n_it = 10
+        xs.zero_()
+        pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        pa.record(stream)
+        iters, rel = fea.fea_pcg(p, values, rhs, xs, q, n_it, 0.0, stream)
+        pb.record(stream)
+        torch.cuda.synchronize()
+        pms = pa.elapsed_time(pb) / max(1, int(iters.max()))
+        # per iteration: the SpMV (values, colind, rowptr, p, Ap) and 13 vector passes of 4 q N bytes
+        pbytes = 4 * q * nnz + 4 * nnz + 8 * (m.n_node + 1) + 2 * 4 * q * m.n_node + 13 * 4 * q * m.n_node
+        out["pcg"] = {"ms_per_iteration": pms, "iterations": int(iters.max()), "rel_resid_max": float(rel.max()),
+                      "algorithmic_bytes_per_iteration": pbytes, "achieved_gbs": pbytes / (pms * 1e-3) / 1e9,
+                      "frac_of_hbm": pbytes / (pms * 1e-3) / 1e9 / hbm_peak,
+                      "system": "MASS + DIFF terms (symmetric positive definite), b = the assembled RHS"}
+        del xs
     if args.residual:
         r = torch.empty((q, m.n_node), dtype=torch.float32, device="cuda")
         ro = fea.fea_default_opts()

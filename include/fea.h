@@ -299,6 +299,23 @@ FEA_API fea_status fea_spmv(const fea_pattern* pattern, const float* values, con
                             int32_t accumulate, void* stream);
 
 /*
+ * fea_pcg -- Jacobi-preconditioned conjugate gradients (Sec. 2, Alg. 1: the algebraic solver
+ * is a preconditioned CG) on the n_eq FP32 matrices assembled on this pattern, each solved
+ * for its own right-hand side: A_q x_q = b_q.  Every A_q must be symmetric positive
+ * definite, e.g. an assembly with the MASS and DIFF terms only.
+ *   values [n_eq][nnz], b [n_eq][n_node] float DEVICE pointers;
+ *   x [n_eq][n_node] float DEVICE pointer: the initial guess in, the solution out.
+ *   Equation q stops when ||b_q - A_q x_q||_2 <= rtol ||b_q||_2 or after max_iter iterations.
+ *   iters [n_eq] (host, may be NULL): iterations taken; rel_resid [n_eq] (host, may be NULL):
+ *   the final ||r_q||_2 / ||b_q||_2 of the recursively updated residual.
+ * The equations iterate together, with FP32 vectors and FP64 scalars.  Runs on `stream` and
+ * waits for it.  A diagonal entry or p.Ap <= 0 stops that equation and returns FEA_ERR_ARG
+ * after the others finish.
+ */
+FEA_API fea_status fea_pcg(const fea_pattern* pattern, const float* values, const float* b, float* x, int32_t n_eq,
+                           int32_t max_iter, double rtol, int32_t* iters, double* rel_resid, void* stream);
+
+/*
  * fea_tuned_strategy -- the scatter (fea_scatter) and equation-group count that
  * FEA_SCATTER_AUTO settled on for this pattern and n_eq.  FEA_ERR_STATE if no FP32
  * FEA_SCATTER_AUTO call has tuned that equation count yet.  Host only; does not wait.

@@ -260,6 +260,16 @@ def apply(elem_type, coords, conn, fields, q, x, terms=ALL_TERMS):
     return y
 
 
+def solve(rowptr, colind, values, b):
+    """The exact solution x = A^-1 b of one assembled system (the result the preconditioned CG
+    of Sec. 2, Alg. 1 converges to), by a sparse direct solve in FP64."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    n = rowptr.size - 1
+    A = sp.csr_matrix((np.asarray(values, np.float64), np.asarray(colind), np.asarray(rowptr)), shape=(n, n))
+    return spla.spsolve(A.tocsc(), np.asarray(b, np.float64))
+
+
 def update_fields(coords, phi, params):
     """One step's field update: returns phi + A sin(k . x + psi) per equation (FP64).
     phi is (n_eq, N); params is (n_eq, 5) = A, kx, ky, kz, psi."""

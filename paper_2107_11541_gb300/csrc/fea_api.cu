@@ -831,6 +831,8 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->inc_local);
   cudaFree(p->ws);
   cudaFree(p->em);
+  cudaFree(p->diag);
+  cudaFree(p->pcg_ws);
   for (auto& kv : p->cancel) cudaFree(kv.second.first);
   plan_destroy(p->plan);
   delete p;

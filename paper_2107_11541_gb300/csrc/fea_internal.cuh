@@ -108,6 +108,10 @@ struct fea_pattern {
   // device workspace for fea_assemble_host
   void* ws;
   size_t ws_bytes;
+  // fea_pcg: diagonal position of every row, and the solver's vectors and scalars
+  int32_t* diag;
+  void* pcg_ws;
+  size_t pcg_bytes;
 };
 
 namespace fea {
@@ -335,6 +339,9 @@ fea_status launch_small_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream
 // FP32 Hex27, one CTA per element, full operator and up to 12 equations (hex27_kernel_applies).
 bool hex27_kernel_applies(const AsmArgs<float>& a);
 fea_status launch_hex27_f32(const AsmArgs<float>& a, cudaStream_t s);
+// y_q = A_q x_q for the n_eq FP32 matrices on pattern p (overwrite or add), on stream s.
+fea_status launch_spmv_f32(const fea_pattern* p, const float* values, const float* x, float* y, int n_eq,
+                           bool accumulate, cudaStream_t s);
 // Row gather of the element matrices in a.em into a.values / a.rhs (overwrite or add).
 fea_status launch_gather_f32(const AsmArgs<float>& a, fea_elem_t type, int maxcol, bool accumulate, cudaStream_t s);
 // Bytes of element-matrix scratch the gather scatter needs.

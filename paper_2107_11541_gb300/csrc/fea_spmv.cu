@@ -38,6 +38,22 @@ __global__ void __launch_bounds__(SPMV_THREADS) k_spmv(const int64_t* __restrict
 }
 
 }  // namespace
+
+fea_status launch_spmv_f32(const fea_pattern* p, const float* values, const float* x, float* y, int n_eq,
+                           bool accumulate, cudaStream_t s) {
+  const int64_t n = p->mesh->n_node;
+  if (n == 0) return FEA_OK;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + SPMV_THREADS - 1) / SPMV_THREADS;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 16));
+  k_spmv<<<grid, SPMV_THREADS, 0, s>>>(p->rowptr, p->colind, values, x, y, n, p->nnz, n_eq, accumulate ? 1 : 0);
+  FEA_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return FEA_OK;
+}
+
 }  // namespace fea
 
 using namespace fea;
@@ -48,18 +64,7 @@ fea_status fea_spmv(const fea_pattern* p, const float* values, const float* x, f
                     int32_t accumulate, void* stream) {
   if (!p || !values || !x || !y) return fail(FEA_ERR_ARG, "fea_spmv: null argument");
   if (n_eq <= 0) return fail(FEA_ERR_ARG, "fea_spmv: n_eq must be > 0 (got %d)", n_eq);
-  const int64_t n = p->mesh->n_node;
-  if (n == 0) return FEA_OK;
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t want = (n + SPMV_THREADS - 1) / SPMV_THREADS;
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 16));
-  k_spmv<<<grid, SPMV_THREADS, 0, (cudaStream_t)stream>>>(p->rowptr, p->colind, values, x, y, n, p->nnz, n_eq,
-                                                          accumulate ? 1 : 0);
-  FEA_CUDA_TRY(cudaGetLastError());
-  count_launches(1);
-  return FEA_OK;
+  return launch_spmv_f32(p, values, x, y, n_eq, accumulate != 0, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -28,7 +28,7 @@ EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_create_mixed", "fea_
            "fea_pattern_build", "fea_pattern_get", "fea_pattern_destroy", "fea_assemble", "fea_residual",
            "fea_assemble_host",
            "fea_pack_plan", "fea_csr_rowptr_noalloc", "fea_update_fields", "fea_graph_capture_steps",
-           "fea_graph_launch", "fea_graph_destroy", "fea_spmv", "fea_tuned_strategy", "fea_cancel_rows", "fea_last_error",
+           "fea_graph_launch", "fea_graph_destroy", "fea_spmv", "fea_pcg", "fea_tuned_strategy", "fea_cancel_rows", "fea_last_error",
            "fea_kernel_launches", "fea_version"]
 
 
@@ -77,6 +77,7 @@ def lib(path: str = LIB_PATH):
         L.fea_graph_launch.argtypes = [vp]
         L.fea_tuned_strategy.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
         L.fea_spmv.argtypes = [vp, vp, vp, vp, i32, i32, vp]
+        L.fea_pcg.argtypes = [vp, vp, vp, vp, i32, i32, dbl, vp, vp, vp]
         L.fea_cancel_rows.argtypes = [vp, i32, C.POINTER(i64)]
         L.fea_graph_destroy.argtypes = [vp]
         L.fea_last_error.restype = C.c_char_p
@@ -240,6 +241,16 @@ def fea_graph_destroy(graph):
 def fea_spmv(pattern, values, x, y, n_eq: int, accumulate: int = 0, stream=None):
     """y[q] = A_q x[q] for all equations (float32 CUDA tensors [n_eq][nnz], [n_eq][N])."""
     _check(lib().fea_spmv(pattern, _ptr(values), _ptr(x), _ptr(y), int(n_eq), int(accumulate), _stream_ptr(stream)))
+
+
+def fea_pcg(pattern, values, b, x, n_eq: int, max_iter: int, rtol: float, stream=None):
+    """Solves A_q x_q = b_q in place (float32 CUDA tensors); returns (iterations, relative residuals)
+    per equation as numpy arrays."""
+    iters = np.zeros(int(n_eq), dtype=np.int32)
+    rel = np.zeros(int(n_eq), dtype=np.float64)
+    _check(lib().fea_pcg(pattern, _ptr(values), _ptr(b), _ptr(x), int(n_eq), int(max_iter), float(rtol),
+                         iters.ctypes.data, rel.ctypes.data, _stream_ptr(stream)))
+    return iters, rel
 
 
 def fea_tuned_strategy(pattern, n_eq: int):
