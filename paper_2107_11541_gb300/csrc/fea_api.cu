@@ -423,6 +423,7 @@ static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, 
   a.dt = dt;
   a.kappa_threshold = o->kappa_threshold;
   a.status = m->status;
+  a.elem_order = (!m->mixed && m->type == FEA_TET4) ? p->elem_order : nullptr;
   return a;
 }
 
@@ -833,6 +834,7 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->em);
   cudaFree(p->diag);
   cudaFree(p->pcg_ws);
+  cudaFree(p->elem_order);
   for (auto& kv : p->cancel) cudaFree(kv.second.first);
   plan_destroy(p->plan);
   delete p;
@@ -928,6 +930,10 @@ fea_status fea_pattern_build(fea_mesh* m, fea_pattern** out) {
   if (e != cudaSuccess) return done(fail(FEA_ERR_CUDA, "pattern launch: %s", cudaGetErrorString(e)));
   st = fea_sync(m);
   if (st != FEA_OK) return done(st);
+  if (!m->mixed && m->type == FEA_TET4) {  // the thread-per-item Tet4 kernel walks elements in this order
+    st = element_order(m, &p->elem_order);
+    if (st != FEA_OK) return done(st);
+  }
   st = plan_build(m, p, &p->plan);
   if (st != FEA_OK) return done(st);
   *out = p;

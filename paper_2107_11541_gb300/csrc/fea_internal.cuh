@@ -108,6 +108,8 @@ struct fea_pattern {
   // device workspace for fea_assemble_host
   void* ws;
   size_t ws_bytes;
+  // locality order of the elements (Tet4 meshes; null otherwise)
+  int32_t* elem_order;
   // fea_pcg: diagonal position of every row, and the solver's vectors and scalars
   int32_t* diag;
   void* pcg_ws;
@@ -284,6 +286,7 @@ __host__ __device__ inline void inv_transpose3(const T J[3][3], T det, T G[3][3]
 template <typename T>
 struct AsmArgs {
   const int32_t* conn;
+  const int32_t* elem_order = nullptr;  // Tet4 atomic kernel: element visit order (null: 0, 1, ...)
   const double* coords;  // [N][3]
   const float* xhi;      // [3][N]
   const float* xlo;      // [3][N]
@@ -339,6 +342,9 @@ fea_status launch_small_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream
 // FP32 Hex27, one CTA per element, full operator and up to 12 equations (hex27_kernel_applies).
 bool hex27_kernel_applies(const AsmArgs<float>& a);
 fea_status launch_hex27_f32(const AsmArgs<float>& a, cudaStream_t s);
+// Morton order of the element centroids (device array of n_elem ids, owned by the caller; null
+// for meshes of several types or fewer than two elements).  Waits for the mesh's stream.
+fea_status element_order(const fea_mesh* m, int32_t** out);
 // y_q = A_q x_q for the n_eq FP32 matrices on pattern p (overwrite or add), on stream s.
 fea_status launch_spmv_f32(const fea_pattern* p, const float* values, const float* x, float* y, int n_eq,
                            bool accumulate, cudaStream_t s);

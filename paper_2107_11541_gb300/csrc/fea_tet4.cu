@@ -9,7 +9,9 @@
 // registers and adds them with atomics into the CSR values and RHS (whose single
 // equation slice of a large Tet4 mesh stays resident in the 129 MB L2), or stores them
 // to the gather scratch.  Gauss points of badly conditioned elements (condition estimate
-// above the threshold, or det <= 0 in FP32) get J^-1 from the FP64 coordinates.
+// above the threshold, or det <= 0 in FP32) get J^-1 from the FP64 coordinates.  Elements
+// are visited in the pattern's Morton order of their centroids, so that the lanes of a warp
+// hold neighbouring elements and their atomics land on few rows.
 #include <algorithm>
 
 #include "fea_internal.cuh"
@@ -28,8 +30,9 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
              t_reac = p.terms & FEA_TERM_REAC, t_supg = p.terms & FEA_TERM_SUPG;
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
        it += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = it / p.eq_count;
-    const int qq = (int)(it - e * p.eq_count), q = p.eq0 + qq;
+    const int64_t eo = it / p.eq_count;
+    const int qq = (int)(it - eo * p.eq_count), q = p.eq0 + qq;
+    const int64_t e = p.elem_order ? (int64_t)__ldg(p.elem_order + eo) : eo;
     int32_t n[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) n[a] = __ldg(p.conn + e * 4 + a);
