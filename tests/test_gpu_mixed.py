@@ -177,3 +177,37 @@ def test_mixed_host_entry_point_and_spmv(mixed):
     torch.cuda.synchronize()
     ref = np.stack([np.add.reduceat(v[k] * x[k][ci].astype(np.float64), rp[:-1]) for k in range(q)])
     assert np.abs(y.cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_mixed_create_edge_cases():
+    """An empty block changes nothing; one block is a single-type mesh; an unknown type, an
+    out-of-range node id and an inverted pyramid are refused with their codes."""
+    mm = G.mixed_mesh(3)
+    run = MixedRun(G.MixedMesh(mm.coords, mm.blocks + [(G.PEN6, np.zeros((0, 6), np.int32))], 3, mm.h))
+    rp, ci, pos = run.pattern_np()
+    orp, oci, opos = O.pattern_mixed(mm.blocks, mm.n_node)
+    assert np.array_equal(rp, orp) and np.array_equal(ci, oci)
+    assert np.array_equal(pos, np.concatenate([q.ravel() for q in opos]))
+    run.close()
+    t, conn = mm.blocks[1]  # the pyramids alone, as one block
+    h1 = fea.fea_mesh_create_mixed(mm.coords, [(t, conn)])
+    p1 = fea.fea_pattern_build(h1)
+    r1, c1, _ = fea.pattern_tensors(p1, mm.n_node, conn.shape[0], G.NEN[t])
+    orp, oci, _ = O.pattern(t, conn, mm.n_node, with_pos=False)
+    assert np.array_equal(r1.cpu().numpy(), orp) and np.array_equal(c1.cpu().numpy(), oci)
+    fea.fea_pattern_destroy(p1)
+    fea.fea_mesh_destroy(h1)
+    bad = [(7, mm.blocks[0][1])] + mm.blocks[1:]
+    with pytest.raises(fea.FeaError) as ei:
+        fea.fea_mesh_create_mixed(mm.coords, bad)
+    assert ei.value.name == "FEA_ERR_ARG"
+    c = mm.blocks[2][1].copy()
+    c[0, 0] = mm.n_node
+    with pytest.raises(fea.FeaError) as ei:
+        fea.fea_mesh_create_mixed(mm.coords, mm.blocks[:2] + [(G.PEN6, c)])
+    assert ei.value.name == "FEA_ERR_RANGE"
+    c = mm.blocks[1][1].copy()
+    c[0, [1, 3]] = c[0, [3, 1]]  # base traversed the other way round: the apex is below it
+    with pytest.raises(fea.FeaError) as ei:
+        fea.fea_mesh_create_mixed(mm.coords, [mm.blocks[0], (G.PYR5, c), mm.blocks[2]])
+    assert ei.value.name == "FEA_ERR_INVERTED"
