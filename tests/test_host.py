@@ -88,3 +88,19 @@ def test_oracle_all_cores_timing():
     assert np.array_equal(coords, m.coords) and np.array_equal(conn, m.conn)
     rates, procs, ne = bench.oracle_all_cores(w, 0.05, 2)
     assert procs >= 1 and 0 < ne <= m.n_elem and len(rates) == 2 and min(rates) > 0
+
+
+def test_mixed_bench_parity_sampler():
+    """The mixed-mesh bench compares sampled rows with the oracle's assembly of the incident
+    elements: the whole mesh's own FP32-rounded assembly passes, and an error planted in one
+    sampled row is reported."""
+    import bench
+    mm, f = bench.make_mixed("mixed_96_4eq", 6)
+    rp, ci, _ = O.pattern_mixed(mm.blocks, mm.n_node, with_pos=False)
+    v, b = O.assemble_mixed(mm.coords, mm.blocks, rp, ci, f.astype(np.float32).astype(np.float64))
+    v32, b32 = v.astype(np.float32), b.astype(np.float32)
+    ok = bench.mixed_parity(mm, f, v32, b32, rp, ci)
+    assert ok["pass"] and ok["max_row_err_A"] < 1e-6
+    bad = v32.copy()
+    bad[0, rp[0]] *= 1.01  # row 0 is always sampled
+    assert not bench.mixed_parity(mm, f, bad, b32, rp, ci)["pass"]
