@@ -1,6 +1,7 @@
 """The cancellation check (opts.cancel_check): flagged rows are recomputed in FP64.
 
-Contrived case: an undistorted Hex8 mesh, SUPG off, phi_old = x - 1/2 for one equation.  The
+Contrived case: an undistorted Hex8 (or prism, or pyramid) mesh, SUPG off, phi_old = x - 1/2 for
+one equation; each mesh is mirror-symmetric about x = 1/2.  The
 RHS of every node on the plane x = 1/2 is then a sum of element contributions that cancel
 (sum |b^e_i| >> |b_i|), so those rows must be flagged; after the FP64 recomputation their
 RHS matches the FP64 oracle to FP64 accuracy relative to the magnitude of the contributions,
@@ -18,18 +19,22 @@ pytestmark = pytest.mark.gpu
 TERMS = fea.FEA_TERM_ALL & ~fea.FEA_TERM_SUPG
 
 
-def contrived(n=8):
-    mesh = G.structured_mesh(G.HEX8, n)
+def contrived(n=8, t=G.HEX8):
+    mesh = G.structured_mesh(t, n)
     rng = np.random.default_rng(3)
     f = G.draw_fields(rng, mesh.coords, 2, 50.0)
     f.phi_old[0] = mesh.coords[:, 0] - 0.5
     return mesh, f.astype(np.float32).astype(np.float64)
 
 
-@pytest.mark.parametrize("scatter", [fea.FEA_SCATTER_ROWOWNED, fea.FEA_SCATTER_GATHER, fea.FEA_SCATTER_ATOMIC])
-def test_cancelling_rows_are_flagged_and_recomputed(scatter):
+@pytest.mark.parametrize("t,scatter", [(G.HEX8, fea.FEA_SCATTER_ROWOWNED), (G.HEX8, fea.FEA_SCATTER_GATHER),
+                                       (G.HEX8, fea.FEA_SCATTER_ATOMIC), (G.PEN6, fea.FEA_SCATTER_GATHER),
+                                       (G.PEN6, fea.FEA_SCATTER_ATOMIC), (G.PYR5, fea.FEA_SCATTER_ATOMIC)],
+                         ids=["hex8_rowowned", "hex8_gather", "hex8_atomic", "pen6_gather", "pen6_atomic",
+                              "pyr5_atomic"])
+def test_cancelling_rows_are_flagged_and_recomputed(t, scatter):
     n = 8
-    mesh, f = contrived(n)
+    mesh, f = contrived(n, t)
     run = GpuRun(mesh)
     try:
         v0, r0 = run.assemble(f, fea.FEA_F32_FUSED, terms=TERMS, scatter=scatter)
