@@ -7,6 +7,7 @@ face integrals of the boundary flux, brute-force dense assembly, and closed-form
 pattern counts.  ``test_pins_catch_planted_mistakes`` plants plausible errors in
 the oracle and checks that every one of them fails at least one pin.
 """
+import functools
 import math
 
 import numpy as np
@@ -176,6 +177,83 @@ def check_box_closed_forms(t):
     assert np.allclose(A, 4.2 * M, rtol=0, atol=1e-12 * 4.2 * scale)
     A, _ = element_terms(t, xe, ue, 0.0, 0.0, phi, 0.25, O.MASS)
     assert np.allclose(A, M / 0.25, rtol=0, atol=1e-12 * scale / 0.25)
+
+
+def check_prism_closed_forms():
+    """A right prism (legs a, b of the triangle in the x-y plane, length c along z): the mass and
+    stiffness matrices are Kronecker products of the linear triangle's and the linear line's
+    (node i + 3k: vertex i of the triangle at end k), which the 3 x 2 rule integrates exactly."""
+    a, b, c = 0.8, 0.5, 1.3
+    tri = np.array([[0, 0], [a, 0], [0, b]], float)
+    xe = np.array([[x, y, z] for z in (0.0, c) for x, y in tri])
+    area = a * b / 2
+    Mt = area / 12 * np.array([[2, 1, 1], [1, 2, 1], [1, 1, 2]])
+    g = np.array([[-1 / a, -1 / b], [1 / a, 0], [0, 1 / b]])  # gradients of the triangle's barycentrics
+    Kt = area * g @ g.T
+    Ml = c / 6 * np.array([[2, 1], [1, 2]])
+    Kl = 1 / c * np.array([[1, -1], [-1, 1]])
+    M = np.kron(Ml, Mt)
+    K = np.kron(Ml, Kt) + np.kron(Kl, Mt)
+    ue = np.zeros((6, 3))
+    phi = np.linspace(0.2, 0.7, 6)
+    A, bb = element_terms(O.PEN6, xe, ue, 0.0, 0.0, phi, 1.0, O.MASS)
+    assert np.allclose(A, M, rtol=0, atol=1e-14 * np.abs(M).max())
+    assert np.allclose(bb, M @ phi, rtol=0, atol=1e-14 * np.abs(M).max())
+    A, _ = element_terms(O.PEN6, xe, ue, 0.6, 0.0, phi, 1.0, O.DIFF)
+    assert np.allclose(A, 0.6 * K, rtol=0, atol=1e-13 * np.abs(K).max())
+
+
+@functools.lru_cache(maxsize=1)
+def pyramid_reference_integrals():
+    """Exact mass and stiffness integrals of the reference pyramid's functions, by sympy in the
+    collapsed coordinates x = r (1 - z), y = t (1 - z) (dx dy dz = (1 - z)^2 dr dt dz), where the
+    functions and their derivatives are polynomials."""
+    import sympy as spy
+    r, t, z = spy.symbols("r t z")
+    sx, sy = [-1, 1, 1, -1], [-1, -1, 1, 1]
+    N, dx, dy, dz = [], [], [], []
+    for a in range(4):  # base corner a, in collapsed form (1 - z)(1 + sx r)(1 + sy t) / 4
+        N.append((1 - z) * (1 + sx[a] * r) * (1 + sy[a] * t) / 4)
+        dx.append((sx[a] + sx[a] * sy[a] * t) / 4)
+        dy.append((sy[a] + sx[a] * sy[a] * r) / 4)
+        dz.append((-1 + sx[a] * sy[a] * r * t) / 4)
+    N.append(z)
+    dx.append(spy.Integer(0))
+    dy.append(spy.Integer(0))
+    dz.append(spy.Integer(1))
+
+    def integral(f):
+        return float(spy.integrate(f * (1 - z) ** 2, (r, -1, 1), (t, -1, 1), (z, 0, 1)))
+    M = np.array([[integral(N[i] * N[j]) for j in range(5)] for i in range(5)])
+    Kxy = np.array([[integral(dx[i] * dx[j] + dy[i] * dy[j]) for j in range(5)] for i in range(5)])
+    Kz = np.array([[integral(dz[i] * dz[j]) for j in range(5)] for i in range(5)])
+    return M, Kxy, Kz
+
+
+def check_pyramid_closed_forms():
+    """An affine pyramid (base [-s, s]^2 at z = 0, apex at height H): mass = s^2 H M_ref and
+    stiffness = H K_xy,ref + (s^2 / H) K_z,ref, from the exact reference integrals."""
+    s_, H = 0.6, 0.9
+    xe = np.array([[-s_, -s_, 0], [s_, -s_, 0], [s_, s_, 0], [-s_, s_, 0], [0, 0, H]], float)
+    Mr, Kxy, Kz = pyramid_reference_integrals()
+    M = s_ * s_ * H * Mr
+    K = H * Kxy + s_ * s_ / H * Kz
+    ue = np.zeros((5, 3))
+    phi = np.linspace(0.1, 0.5, 5)
+    A, bb = element_terms(O.PYR5, xe, ue, 0.0, 0.0, phi, 1.0, O.MASS)
+    assert np.allclose(A, M, rtol=0, atol=1e-14 * np.abs(M).max())
+    assert np.allclose(bb, M @ phi, rtol=0, atol=1e-14 * np.abs(M).max())
+    A, _ = element_terms(O.PYR5, xe, ue, 0.45, 0.0, phi, 1.0, O.DIFF)
+    assert np.allclose(A, 0.45 * K, rtol=0, atol=1e-13 * np.abs(K).max())
+
+
+def test_prism_closed_forms():
+    check_prism_closed_forms()
+
+
+def test_pyramid_closed_forms():
+    pytest.importorskip("sympy")
+    check_pyramid_closed_forms()
 
 
 def random_tet(rng):
@@ -634,7 +712,7 @@ def all_pins():
                  lambda t=t: check_scaling_translation(t)]
     pins += [lambda: check_box_closed_forms(O.HEX8), lambda: check_box_closed_forms(O.HEX27),
              lambda: check_tet_closed_forms(np.random.default_rng(7)), check_pattern_counts,
-             lambda: check_bruteforce(O.HEX8), check_mixed]
+             lambda: check_bruteforce(O.HEX8), check_mixed, check_prism_closed_forms, check_pyramid_closed_forms]
     pins += [lambda t=t, fr=fr: check_patch(t, fr) for t, fr in PATCH]
     return pins
 
