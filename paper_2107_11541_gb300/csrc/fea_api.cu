@@ -438,14 +438,16 @@ struct Strategy {
   int groups;   // equation groups of the row-owned scatter
 };
 
-// FP32 element-parallel launch over every element block: the batched Hex8 kernel where the
-// mesh has its schedule (single-type Hex8), else the per-type kernels behind launch_generic_f32.
-fea_status elem_f32(fea_mesh* m, const fea_pattern* p, const AsmArgs<float>& a0, cudaStream_t s) {
+// FP32 element-parallel launch over every element block: the batched Hex8 kernel for Hex8
+// blocks (its node-major field scratch held by the plan of a single-type mesh, else by the
+// pattern), the per-type kernels behind launch_generic_f32 for the others.
+fea_status elem_f32(fea_mesh* m, fea_pattern* p, const AsmArgs<float>& a0, cudaStream_t s) {
   for (const fea_mesh::Block& b : m->blocks) {
     if (b.n_elem == 0) continue;
     AsmArgs<float> a = a0;
     set_block(a, b, p);
     if (b.type == FEA_HEX8 && p->plan) FEA_TRY(plan_elem(p->plan, a, s));
+    else if (b.type == FEA_HEX8) FEA_TRY(hex8_elem(p->hex8_fnode, p->hex8_fnode_bytes, a, s));
     else FEA_TRY(launch_generic_f32(a, b.type, s));
   }
   return FEA_OK;
@@ -835,6 +837,7 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->diag);
   cudaFree(p->pcg_ws);
   cudaFree(p->elem_order);
+  cudaFree(p->hex8_fnode);
   for (auto& kv : p->cancel) cudaFree(kv.second.first);
   plan_destroy(p->plan);
   delete p;
@@ -994,7 +997,7 @@ fea_status fea_residual(fea_mesh* m, const fea_pattern* p, const void* vel, cons
       AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi_old, dt, n_eq, &o, nullptr, nullptr);
       a.phi_eval = (const float*)phi;
       a.resid = (float*)r;
-      FEA_TRY(elem_f32(m, p, a, s));
+      FEA_TRY(elem_f32(m, const_cast<fea_pattern*>(p), a, s));  // the field scratch belongs to the pattern
     }
   }
   if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, s));

@@ -114,6 +114,9 @@ struct fea_pattern {
   int32_t* diag;
   void* pcg_ws;
   size_t pcg_bytes;
+  // node-major fields for the batched Hex8 kernel on the Hex8 block of a mixed mesh
+  float* hex8_fnode;
+  size_t hex8_fnode_bytes;
 };
 
 namespace fea {

@@ -19,6 +19,9 @@ int plan_group_size(int n_eq, int groups);
 // Element-parallel FP32 Hex8 (no schedule): atomics, the gather scratch (a.em) or the
 // matrix-free residual (a.resid), for the launch's equations.
 fea_status plan_elem(fea_rowowned_plan* plan, const AsmArgs<float>& a, cudaStream_t s);
+// The same kernel with the node-major field scratch held by the caller (grown on demand):
+// the Hex8 block of a mixed mesh, which has no plan.
+fea_status hex8_elem(float*& fnode, size_t& fnode_bytes, const AsmArgs<float>& a, cudaStream_t s);
 // Frees the schedules of every group size not listed in keep.
 void plan_trim(fea_rowowned_plan* plan, const std::vector<int>& keep);
 

@@ -544,33 +544,33 @@ static fea_status assemble_group(ro::Variant* v, const AsmArgs<float>& a, int ac
   return FEA_OK;
 }
 
-fea_status plan_elem(fea_rowowned_plan* P, const AsmArgs<float>& a, cudaStream_t s) {
-  // node-major fields of all the launch's equations, in a scratch owned by the plan
+fea_status hex8_elem(float*& fnode, size_t& fnode_bytes, const AsmArgs<float>& a, cudaStream_t s) {
+  // node-major fields of all the launch's equations, in the caller's scratch (grown here)
   const int rec = 3 * a.eq_count + 3;
   const size_t need = sizeof(float) * (size_t)a.n_node * rec;
-  if (P->elem_fnode_bytes < need) {
+  if (fnode_bytes < need) {
     FEA_CUDA_TRY(cudaStreamSynchronize(s));
-    cudaFree(P->elem_fnode);
-    P->elem_fnode = nullptr;
-    P->elem_fnode_bytes = 0;
-    if (cudaMalloc(&P->elem_fnode, need) != cudaSuccess) {
+    cudaFree(fnode);
+    fnode = nullptr;
+    fnode_bytes = 0;
+    if (cudaMalloc(&fnode, need) != cudaSuccess) {
       cudaGetLastError();
       return fail(FEA_ERR_OOM, "element kernel: %zu bytes of node-major fields", need);
     }
-    P->elem_fnode_bytes = need;
+    fnode_bytes = need;
   }
   const int64_t fo = (int64_t)a.eq0 * a.n_node;
   {
     const size_t tsm = sizeof(float) * rec * 33;
     FEA_CUDA_TRY(cudaFuncSetAttribute(ro::k_fields_nodemajor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
     ro::k_fields_nodemajor<<<(unsigned)((a.n_node + 31) / 32), 256, tsm, s>>>(a.kd + fo, a.sr + fo, a.phi + fo, a.vel,
-                                                                              a.n_node, a.eq_count, P->elem_fnode);
+                                                                              a.n_node, a.eq_count, fnode);
     FEA_CUDA_TRY(cudaGetLastError());
     count_launches(1);
   }
   ro::RoArgs r{};
   r.a = a;
-  r.fnode = P->elem_fnode;
+  r.fnode = fnode;
   r.rec = rec;
   r.be = ro::batch_elems(a.eq_count);
   const size_t smem = sizeof(float) * (size_t)r.be * (ro::GEO_ELEM + ro::NEN * ro::RAW + ro::NEN);
@@ -592,6 +592,10 @@ fea_status plan_elem(fea_rowowned_plan* P, const AsmArgs<float>& a, cudaStream_t
   FEA_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return FEA_OK;
+}
+
+fea_status plan_elem(fea_rowowned_plan* P, const AsmArgs<float>& a, cudaStream_t s) {
+  return hex8_elem(P->elem_fnode, P->elem_fnode_bytes, a, s);
 }
 
 fea_status plan_assemble(fea_rowowned_plan* P, const AsmArgs<float>& a, int accumulate, int groups, cudaStream_t s) {

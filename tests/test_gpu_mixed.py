@@ -211,3 +211,52 @@ def test_mixed_create_edge_cases():
     with pytest.raises(fea.FeaError) as ei:
         fea.fea_mesh_create_mixed(mm.coords, [mm.blocks[0], (G.PYR5, c), mm.blocks[2]])
     assert ei.value.name == "FEA_ERR_INVERTED"
+
+
+@pytest.mark.parametrize("terms,accumulate", [(fea.FEA_TERM_ALL, 0), (fea.FEA_TERM_MASS | fea.FEA_TERM_DIFF, 1),
+                                              (fea.FEA_TERM_CONV | fea.FEA_TERM_SUPG | fea.FEA_TERM_REAC, 0)],
+                         ids=["all", "mass_diff_accumulate", "conv_supg_reac"])
+def test_mixed_hex_block_many_equations(terms, accumulate):
+    """The Hex8 block of a mixed mesh goes through the batched Hex8 kernel: 13 equations (a
+    batch of 19 elements, so the block's 98 end in a batch of 3), a subset of the terms, and the
+    accumulate flag (two calls add up to twice the operator); then the residual of the same
+    system."""
+    mm = G.mixed_mesh(7)
+    G.perturb_interior(mm, np.random.default_rng(12), 0.1)
+    f = fields_for(mm.coords, 13, 13)
+    run = MixedRun(mm)
+    torch = run.torch
+    try:
+        q = f.n_eq
+        args = run.upload(f, fea.FEA_F32_FUSED)
+        vals = torch.zeros((q, run.nnz), device="cuda")
+        rhs = torch.zeros((q, mm.n_node), device="cuda")
+        opts = fea.fea_default_opts(terms=terms, accumulate=accumulate)
+        for _ in range(2 if accumulate else 1):
+            fea.fea_assemble(run.handle, run.pattern, *args, f.dt, q, opts, vals, rhs)
+        fea.fea_sync(run.handle)
+        scale = 2.0 if accumulate else 1.0
+        v = vals.cpu().numpy().astype(np.float64) / scale
+        r = rhs.cpu().numpy().astype(np.float64) / scale
+        rp, ci, _ = O.pattern_mixed(mm.blocks, mm.n_node, with_pos=False)
+        wide = widen(f, fea.FEA_F32_FUSED)
+        ref, refb, _, absb = O.assemble_mixed(mm.coords, mm.blocks, rp, ci, wide, terms=terms, with_abs=True)
+        ea, eb = row_errors(rp, v, ref).max(), rhs_errors(r, refb, absb).max()
+        assert ea <= TOL_F32 and eb <= TOL_F32, (ea, eb)
+        if terms != fea.FEA_TERM_ALL:
+            return
+        phi = np.random.default_rng(14).uniform(0, 1, (q, mm.n_node)).astype(np.float32)
+        res = torch.full((q, mm.n_node), float("nan"), device="cuda")
+        fea.fea_residual(run.handle, run.pattern, *args, torch.from_numpy(phi).cuda(), f.dt, q,
+                         fea.fea_default_opts(), res)
+        fea.fea_sync(run.handle)
+        got = res.cpu().numpy().astype(np.float64)
+        _, b, absA, absb = O.assemble_mixed(mm.coords, mm.blocks, rp, ci, wide, with_abs=True)
+        rows = np.repeat(np.arange(mm.n_node), np.diff(rp))
+        ph = phi.astype(np.float64)
+        for k in range(q):
+            ref_r = b[k] - O.apply_mixed(mm.coords, mm.blocks, wide, k, ph[k])
+            sc = absb[k] + np.bincount(rows, weights=absA[k] * np.abs(ph[k][ci]), minlength=mm.n_node)
+            assert (np.abs(got[k] - ref_r) / np.where(sc > 0, sc, 1.0)).max() <= TOL_F32
+    finally:
+        run.close()
