@@ -303,6 +303,8 @@ def main():
                     help="also time the batched SpMV y_q = A_q x_q (fea_spmv) on the assembled matrices")
     ap.add_argument("--pcg", action="store_true",
                     help="also time the batched Jacobi-preconditioned CG (fea_pcg) on the MASS + DIFF matrices")
+    ap.add_argument("--laplacian", action="store_true",
+                    help="also time the Laplacian of the same mesh (the DIFF term alone, k = 1, one equation)")
     ap.add_argument("--graph", type=int, default=None,
                     help="1: time the K steps as one CUDA graph of K (assemble, field update) time steps "
                          "(default on for hex8_256_32eq)")
@@ -485,6 +487,36 @@ def main():
                       "frac_of_hbm": pbytes / (pms * 1e-3) / 1e9 / hbm_peak,
                       "system": "MASS + DIFF terms (symmetric positive definite), b = the assembled RHS"}
         del xs
+    if args.laplacian:
+        # the Laplacian of the same mesh: the diffusion term alone with k = 1, one equation (Algorithm 1
+        # assembles it once per run); the first call also tunes the scatter for one equation
+        lf = G.Fields(np.zeros((3, m.n_node)), np.ones((1, m.n_node)), np.zeros((1, m.n_node)),
+                      np.zeros((1, m.n_node)), 1.0)
+        ld = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+              for a in (lf.velocity, lf.diffusivity, lf.reaction, lf.phi_old)]
+        lv = torch.empty((1, nnz), dtype=torch.float32, device="cuda")
+        lr = torch.empty((1, m.n_node), dtype=torch.float32, device="cuda")
+        lo = fea.fea_default_opts(terms=fea.FEA_TERM_DIFF, scatter=args.scatter)
+        fea.fea_assemble(h, p, *ld, lf.dt, 1, lo, lv, lr)
+        fea.fea_sync(h)
+        la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        la.record(stream)
+        for _ in range(5):
+            fea.fea_assemble(h, p, *ld, lf.dt, 1, lo, lv, lr)
+        lb.record(stream)
+        torch.cuda.synchronize()
+        lms = la.elapsed_time(lb) / 5
+        out["laplacian"] = {"ms": lms, "value": m.n_elem / (lms * 1e-3), "unit": "elements/s",
+                            "what": "K = sum_e int grad N_a . grad N_b (DIFF term, k = 1), FP32, one equation"}
+        try:
+            sc, _ = fea.fea_tuned_strategy(p, 1)
+            out["laplacian"]["scatter"] = {1: "atomic", 2: "rowowned", 3: "gather"}.get(sc, str(sc))
+        except fea.FeaError:
+            pass
+        if rank == 0 and not args.no_parity:
+            out["laplacian"]["parity"] = sampled_parity(G.Workload(w.name, m, lf, w.precision), lv, lr, p, nnz,
+                                                        terms=fea.FEA_TERM_DIFF)
+        del ld, lv, lr
     if args.residual:
         r = torch.empty((q, m.n_node), dtype=torch.float32, device="cuda")
         ro = fea.fea_default_opts()
@@ -698,14 +730,15 @@ def run_mixed(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def sampled_parity(w, values, rhs, p, nnz, n_rows=48, seed=5):
+def sampled_parity(w, values, rhs, p, nnz, n_rows=48, seed=5, terms=None):
     """Sampled full-size rows against the oracle (computed row by row from incident elements)."""
     import oracle as O
     from paper_2107_11541_gb300 import fea
     m = w.mesh
     rp_t, ci_t, _ = fea.pattern_tensors(p, m.n_node, 0, NEN[m.elem_type])
     rp = rp_t.cpu().numpy()
-    rs = O.RowSampler(m.elem_type, m.coords, m.conn, w.fields.astype(np.float32).astype(np.float64))
+    rs = O.RowSampler(m.elem_type, m.coords, m.conn, w.fields.astype(np.float32).astype(np.float64),
+                      O.ALL_TERMS if terms is None else terms)
     rng = np.random.default_rng(seed)
     rows = np.unique(np.concatenate([[0, m.n_node - 1], rng.integers(0, m.n_node, n_rows)]))
     worst_a = worst_b = 0.0

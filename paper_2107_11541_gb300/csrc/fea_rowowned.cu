@@ -67,6 +67,15 @@ static int batch_elems(int n_eq) {
   return std::max(1, std::min(BEMAX, THREADS / n_eq));
 }
 
+// Batch size of the element-parallel kernel: the same rule with a larger cap, so that with few
+// equations the (element, equation) items still fill the CTA (its geometry runs in passes of
+// THREADS / NG elements).  The cap keeps the batch's shared memory within one CTA's share.
+static int elem_batch(int n_eq, int cap) {
+  int be2 = std::max(1, std::min(cap, 2 * THREADS / n_eq));
+  if (be2 * n_eq >= (2 * THREADS * 85) / 100) return be2;
+  return std::max(1, std::min(cap, THREADS / n_eq));
+}
+
 // Shared memory besides the row window, for batches of `be` elements.
 // Geometry of a batch plus two staging buffers (raw node data, node ids, offsets).
 static size_t smem_fixed(int be) {
@@ -572,9 +581,10 @@ fea_status hex8_elem(float*& fnode, size_t& fnode_bytes, const AsmArgs<float>& a
   r.a = a;
   r.fnode = fnode;
   r.rec = rec;
-  r.be = ro::batch_elems(a.eq_count);
-  const size_t smem = sizeof(float) * (size_t)r.be * (ro::GEO_ELEM + ro::NEN * ro::RAW + ro::NEN);
   const bool full = a.terms == FEA_TERM_ALL;
+  // 96 elements take 180 KB; the residual kernel of the full operator runs two CTAs per SM: 48
+  r.be = ro::elem_batch(a.eq_count, a.resid && full ? 48 : 96);
+  const size_t smem = sizeof(float) * (size_t)r.be * (ro::GEO_ELEM + ro::NEN * ro::RAW + ro::NEN);
   auto pick = [&](auto full_k, auto part_k) { return full ? full_k : part_k; };
   void (*kern)(ro::RoArgs) =
       a.resid ? pick(ro::k_hex8_elem<true, ro::EMODE_RESIDUAL>, ro::k_hex8_elem<false, ro::EMODE_RESIDUAL>)

@@ -536,8 +536,12 @@ __global__ void __launch_bounds__(THREADS, (MODE == EMODE_RESIDUAL && FULL) ? 2 
                                                             : r.fnode[n * r.rec + 3 * n_eq + (c - 6)];
     }
     __syncthreads();
-    const int gw = (nv * NG + 31) / 32;
-    if (warp < gw) geometry(r, S, geo, tid >> 3, tid & 7, (tid >> 3) < nv);
+    // one thread per (element, Gauss point), THREADS / NG elements per pass; a warp takes part in a
+    // pass when it holds one of the batch's elements (the shuffles inside span the whole warp)
+    for (int eb = 0; eb < nv; eb += THREADS / NG) {
+      const int ge = eb + (tid >> 3);
+      if (eb + warp * (32 / NG) < nv) geometry(r, S, geo, ge, tid & 7, ge < nv);
+    }
     __syncthreads();
     const int items = nv * n_eq;
     for (int item = tid; item < items; item += THREADS) {

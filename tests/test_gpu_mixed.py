@@ -218,7 +218,7 @@ def test_mixed_create_edge_cases():
                          ids=["all", "mass_diff_accumulate", "conv_supg_reac"])
 def test_mixed_hex_block_many_equations(terms, accumulate):
     """The Hex8 block of a mixed mesh goes through the batched Hex8 kernel: 13 equations (a
-    batch of 19 elements, so the block's 98 end in a batch of 3), a subset of the terms, and the
+    batch of 39 elements, so the block's 98 end in a batch of 20), a subset of the terms, and the
     accumulate flag (two calls add up to twice the operator); then the residual of the same
     system."""
     mm = G.mixed_mesh(7)
