@@ -104,3 +104,36 @@ def test_mixed_bench_parity_sampler():
     bad = v32.copy()
     bad[0, rp[0]] *= 1.01  # row 0 is always sampled
     assert not bench.mixed_parity(mm, f, bad, b32, rp, ci)["pass"]
+
+
+def test_roofline_unit_figures():
+    """The algorithmic bytes and flops behind the bench's roofline fractions.  Bytes: connectivity,
+    coordinates and velocity, per-equation k, s and phi, and the CSR values and RHS written once,
+    for the 10^3 Tet4 case in FP64 (0.34 MB) and the Hex8 128^3 x 21 workload in FP32 (5.63 GB), from
+    the closed-form node, element and nonzero counts of the structured meshes.  Flops: the
+    multiply-adds of the direct form per element and equation, counted term by term here."""
+    import bench
+
+    def counted(nen, ng):  # one multiply-add = 2 flops
+        madds = 0
+        for _g in range(ng):
+            madds += nen * nen                                    # rank-1 Galerkin/SUPG product P_a Q_b
+            madds += sum(1 for a in range(nen) for b in range(a, nen))  # symmetric diffusion grad N_a . grad N_b
+            madds += 6 * nen  # u_g (3), k_g, s_g, phi_g interpolation, each nen long
+        return 2 * madds
+
+    for t, ng, want in ((G.TET4, 4, 400), (G.HEX8, 8, 2368), (G.HEX27, 27, 68526), (G.PEN6, 6, 1116),
+                        (G.PYR5, 12, 1680)):
+        nen = G.NEN[t]
+        assert bench.algorithmic_flops_per_elem_eq(nen, ng) == counted(nen, ng) == want
+    # Kuhn 10^3: E = 6 n^3, N = (n+1)^3, nnz = N + 2 (edges), edges = 3n(n+1)^2 + 3n^2(n+1) + n^3
+    n = 10
+    E, N = 6 * n ** 3, (n + 1) ** 3
+    nnz = N + 2 * (3 * n * (n + 1) ** 2 + 3 * n ** 2 * (n + 1) + n ** 3)
+    assert nnz == 17191
+    assert bench.algorithmic_bytes(E, N, nnz, 4, 1, s=8) == 340008
+    # Hex8 128^3: nnz = (sum of 1-D row lengths)^3 = (3 * 129 - 2)^3
+    n = 128
+    E, N, nnz = n ** 3, (n + 1) ** 3, (3 * (n + 1) - 2) ** 3
+    assert nnz == 57066625
+    assert bench.algorithmic_bytes(E, N, nnz, 8, 21) == 5633513404
