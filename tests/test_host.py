@@ -137,3 +137,32 @@ def test_roofline_unit_figures():
     E, N, nnz = n ** 3, (n + 1) ** 3, (3 * (n + 1) - 2) ** 3
     assert nnz == 57066625
     assert bench.algorithmic_bytes(E, N, nnz, 8, 21) == 5633513404
+
+
+def test_reference_arm_line_and_other_ranks():
+    """bench.py --impl reference: rank 0 prints one JSON line with the oracle timed on the host
+    cores (a shrunken Hex8 case here); any other rank exits 0 without output."""
+    import json
+    import subprocess
+    import sys
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--cells", "4", "--steps", "2",
+           "--warmup", "1"]
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["metric"] == bench_metric() and d["unit"] == "elem*eq/s" and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["value"] == d["value"] == d["e2e"]["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def bench_metric():
+    import bench
+    return bench.METRIC
