@@ -166,3 +166,24 @@ def test_reference_arm_line_and_other_ranks():
 def bench_metric():
     import bench
     return bench.METRIC
+
+
+def test_profiled_traffic_goes_null_when_the_kernels_change(tmp_path, monkeypatch):
+    """bench.py reports the DRAM traffic of a committed ncu summary only while the kernel
+    sources hash to the digest recorded with it; after any change to them it reports null."""
+    import shutil
+
+    import bench
+    src = os.path.join(ROOT, "paper_2107_11541_gb300", "csrc")
+    csrc = tmp_path / "paper_2107_11541_gb300" / "csrc"
+    shutil.copytree(src, csrc)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    digest = bench.kernel_source_digest()
+    (tmp_path / "profiles" / "dram_traffic_w.txt").write_text(
+        "# a comment: with colons\ntraffic_bytes_per_launch: 1234\nkernel_source_digest: %s\n" % digest)
+    assert bench.profiled_traffic("w") == 1234.0
+    assert bench.profiled_traffic("absent") is None
+    with open(csrc / "fea_api.cu", "a") as f:
+        f.write("\n")
+    assert bench.kernel_source_digest() != digest and bench.profiled_traffic("w") is None
