@@ -247,6 +247,68 @@ def check_pyramid_closed_forms():
     assert np.allclose(A, 0.45 * K, rtol=0, atol=1e-13 * np.abs(K).max())
 
 
+def lagrange_1d_from_roots(q):
+    """The 1-D Lagrange bases on q equispaced nodes of [-1, 1] (q = 2 or 3), built from their
+    roots, with their derivatives."""
+    nodes = np.linspace(-1.0, 1.0, q)
+    basis = []
+    for i in range(q):
+        others = np.delete(nodes, i)
+        p = np.poly1d(others, r=True) / np.prod(nodes[i] - others)
+        basis.append((p, p.deriv()))
+    return nodes, basis
+
+
+def check_affine_hex_high_order(t, seed=4):
+    """An affine, sheared hexahedron x = F xi + c with constant u, k and s: every term of the
+    operator is then a polynomial that the element's own Gauss rule integrates exactly, so the
+    oracle's matrix and RHS must equal an integration with 5 Gauss-Legendre points per axis
+    (exact to degree 9), formed here from tensor-product Lagrange bases and F^-T (F is not
+    symmetric, unlike a box's Jacobian)."""
+    rng = np.random.default_rng(seed)
+    q = 2 if t == O.HEX8 else 3
+    order = q - 1
+    F = np.eye(3) * 0.6 + rng.uniform(-0.15, 0.15, (3, 3))
+    assert np.linalg.det(F) > 0.1
+    c = rng.uniform(-1, 1, 3)
+    nodes, basis = lagrange_1d_from_roots(q)
+    idx = [(i, j, k) for k in range(q) for j in range(q) for i in range(q)]
+    xe = np.array([F @ np.array([nodes[i], nodes[j], nodes[k]]) + c for i, j, k in idx])
+    nen = len(idx)
+    u = np.array([0.7, -0.35, 0.5])
+    kd, sr, dt = 0.08, 3.0, 0.05
+    phi = rng.uniform(0, 1, nen)
+    det = np.linalg.det(F)
+    Ginv = np.linalg.inv(F).T
+    h = (8.0 * det) ** (1.0 / 3.0) / order
+    tau = 1.0 / (4.0 * kd / h ** 2 + 2.0 * np.linalg.norm(u) / h + sr)
+    gx, gw = np.polynomial.legendre.leggauss(5)
+    A = np.zeros((nen, nen))
+    b = np.zeros(nen)
+    for a1, w1 in zip(gx, gw):
+        for a2, w2 in zip(gx, gw):
+            for a3, w3 in zip(gx, gw):
+                xi = (a1, a2, a3)
+                N = np.array([basis[i][0](xi[0]) * basis[j][0](xi[1]) * basis[k][0](xi[2]) for i, j, k in idx])
+                dN = np.array([[basis[i][1](xi[0]) * basis[j][0](xi[1]) * basis[k][0](xi[2]),
+                                basis[i][0](xi[0]) * basis[j][1](xi[1]) * basis[k][0](xi[2]),
+                                basis[i][0](xi[0]) * basis[j][0](xi[1]) * basis[k][1](xi[2])] for i, j, k in idx])
+                grad = dN @ Ginv.T  # row a: F^-T grad_xi N_a
+                ua = grad @ u
+                dV = w1 * w2 * w3 * det
+                A += dV * (np.outer(N, N) / dt + np.outer(N, ua) + kd * grad @ grad.T + sr * np.outer(N, N)
+                           + tau * np.outer(ua, N / dt + ua + sr * N))
+                b += dV * (N + tau * ua) * (N @ phi) / dt
+    Ao, bo = element_terms(t, xe, np.tile(u, (nen, 1)), kd, sr, phi, dt, O.ALL_TERMS)
+    assert np.abs(Ao - A).max() <= 1e-12 * np.abs(A).max()
+    assert np.abs(bo - b).max() <= 1e-12 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("t", (O.HEX8, O.HEX27))
+def test_affine_hex_matches_high_order_rule(t):
+    check_affine_hex_high_order(t)
+
+
 def test_prism_closed_forms():
     check_prism_closed_forms()
 
@@ -712,7 +774,8 @@ def all_pins():
                  lambda t=t: check_scaling_translation(t)]
     pins += [lambda: check_box_closed_forms(O.HEX8), lambda: check_box_closed_forms(O.HEX27),
              lambda: check_tet_closed_forms(np.random.default_rng(7)), check_pattern_counts,
-             lambda: check_bruteforce(O.HEX8), check_mixed, check_prism_closed_forms]
+             lambda: check_bruteforce(O.HEX8), check_mixed, check_prism_closed_forms,
+             lambda: check_affine_hex_high_order(O.HEX8), lambda: check_affine_hex_high_order(O.HEX27)]
     try:
         import sympy  # noqa: F401  (the pyramid's exact integrals)
         pins.append(check_pyramid_closed_forms)
