@@ -259,54 +259,108 @@ def lagrange_1d_from_roots(q):
     return nodes, basis
 
 
-def check_affine_hex_high_order(t, seed=4):
-    """An affine, sheared hexahedron x = F xi + c with constant u, k and s: every term of the
-    operator is then a polynomial that the element's own Gauss rule integrates exactly, so the
-    oracle's matrix and RHS must equal an integration with 5 Gauss-Legendre points per axis
-    (exact to degree 9), formed here from tensor-product Lagrange bases and F^-T (F is not
-    symmetric, unlike a box's Jacobian)."""
+def gl01(n):
+    """n-point Gauss-Legendre rule on [0, 1]."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    return (x + 1.0) / 2.0, w / 2.0
+
+
+def high_order_points(t):
+    """Points of a high-order rule on the reference element, as (weight, N, grad_xi N): tensor
+    Gauss-Legendre for the hexahedra; the tetrahedron, the prism's triangle and the pyramid
+    integrated in collapsed (Duffy) coordinates, where the integrands of affine elements are
+    polynomials.  The shape functions are written here from their definitions (tensor-product
+    Lagrange bases; barycentrics; triangle x line; the pyramid's functions in collapsed form)."""
+    pts = []
+    g5, w5 = np.polynomial.legendre.leggauss(5)
+    r6, w6 = gl01(6)
+    if t in (O.HEX8, O.HEX27):
+        q = 2 if t == O.HEX8 else 3
+        _, basis = lagrange_1d_from_roots(q)
+        idx = [(i, j, k) for k in range(q) for j in range(q) for i in range(q)]
+        for a1, w1 in zip(g5, w5):
+            for a2, w2 in zip(g5, w5):
+                for a3, w3 in zip(g5, w5):
+                    xi = (a1, a2, a3)
+                    v = [[basis[i][d == 0](xi[0]) * basis[j][d == 1](xi[1]) * basis[k][d == 2](xi[2])
+                          for i, j, k in idx] for d in (-1, 0, 1, 2)]
+                    pts.append((w1 * w2 * w3, np.array(v[0]), np.array(v[1:]).T))
+    elif t == O.TET4:  # xi = a, eta = b (1 - a), zeta = c (1 - a)(1 - b)
+        dN = np.array([[-1, -1, -1], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+        for a, wa in zip(r6, w6):
+            for b, wb in zip(r6, w6):
+                for c, wc in zip(r6, w6):
+                    x, y, z = a, b * (1 - a), c * (1 - a) * (1 - b)
+                    pts.append((wa * wb * wc * (1 - a) ** 2 * (1 - b), np.array([1 - x - y - z, x, y, z]), dN))
+    elif t == O.PEN6:  # triangle (xi, eta) = (a, b (1 - a)) times zeta in [-1, 1]
+        for a, wa in zip(r6, w6):
+            for b, wb in zip(r6, w6):
+                x, y = a, b * (1 - a)
+                L = np.array([1 - x - y, x, y])
+                dL = np.array([[-1, -1], [1, 0], [0, 1]], float)
+                for z, wz in zip(g5, w5):
+                    lo, hi = (1 - z) / 2, (1 + z) / 2
+                    N = np.concatenate([L * lo, L * hi])
+                    dN = np.vstack([np.column_stack([dL * lo, -L / 2]), np.column_stack([dL * hi, L / 2])])
+                    pts.append((wa * wb * wz * (1 - a), N, dN))
+    else:  # pyramid: x = r (1 - z), y = s (1 - z), dV = (1 - z)^2 dr ds dz
+        sx, sy = np.array([-1, 1, 1, -1.0]), np.array([-1, -1, 1, 1.0])
+        for r, wr in zip(g5, w5):
+            for s_, ws in zip(g5, w5):
+                for z, wz in zip(r6, w6):
+                    N = np.append((1 - z) * (1 + sx * r) * (1 + sy * s_) / 4, z)
+                    dN = np.vstack([np.column_stack([(sx + sx * sy * s_) / 4, (sy + sx * sy * r) / 4,
+                                                     (-1 + sx * sy * r * s_) / 4]), [0.0, 0.0, 1.0]])
+                    pts.append((wr * ws * wz * (1 - z) ** 2, N, dN))
+    return pts
+
+
+def exact_ref_nodes(t):
+    nodes = ref_nodes(t)
+    if t == O.PYR5:
+        nodes[4, 2] = 1.0
+    return nodes
+
+
+def check_affine_high_order(t, seed=4):
+    """An affine, sheared element x = F xi + c with constant u, k and s: every term of the
+    operator is then a polynomial (in collapsed coordinates for the tetrahedron, the prism's
+    triangle and the pyramid) that the element's own rule integrates exactly, so the oracle's
+    matrix and RHS must equal the same integrand under a rule of much higher order.  F is not
+    symmetric, unlike a box's Jacobian, so F^-T and F^-1 differ."""
     rng = np.random.default_rng(seed)
-    q = 2 if t == O.HEX8 else 3
-    order = q - 1
+    order = 2 if t == O.HEX27 else 1
     F = np.eye(3) * 0.6 + rng.uniform(-0.15, 0.15, (3, 3))
     assert np.linalg.det(F) > 0.1
     c = rng.uniform(-1, 1, 3)
-    nodes, basis = lagrange_1d_from_roots(q)
-    idx = [(i, j, k) for k in range(q) for j in range(q) for i in range(q)]
-    xe = np.array([F @ np.array([nodes[i], nodes[j], nodes[k]]) + c for i, j, k in idx])
-    nen = len(idx)
+    xe = exact_ref_nodes(t) @ F.T + c
+    nen = xe.shape[0]
     u = np.array([0.7, -0.35, 0.5])
     kd, sr, dt = 0.08, 3.0, 0.05
     phi = rng.uniform(0, 1, nen)
     det = np.linalg.det(F)
     Ginv = np.linalg.inv(F).T
-    h = (8.0 * det) ** (1.0 / 3.0) / order
+    pts = high_order_points(t)
+    assert abs(sum(w for w, _, _ in pts) - REF_VOLUME[t]) < 1e-13
+    h = (REF_VOLUME[t] * det) ** (1.0 / 3.0) / order
     tau = 1.0 / (4.0 * kd / h ** 2 + 2.0 * np.linalg.norm(u) / h + sr)
-    gx, gw = np.polynomial.legendre.leggauss(5)
     A = np.zeros((nen, nen))
     b = np.zeros(nen)
-    for a1, w1 in zip(gx, gw):
-        for a2, w2 in zip(gx, gw):
-            for a3, w3 in zip(gx, gw):
-                xi = (a1, a2, a3)
-                N = np.array([basis[i][0](xi[0]) * basis[j][0](xi[1]) * basis[k][0](xi[2]) for i, j, k in idx])
-                dN = np.array([[basis[i][1](xi[0]) * basis[j][0](xi[1]) * basis[k][0](xi[2]),
-                                basis[i][0](xi[0]) * basis[j][1](xi[1]) * basis[k][0](xi[2]),
-                                basis[i][0](xi[0]) * basis[j][0](xi[1]) * basis[k][1](xi[2])] for i, j, k in idx])
-                grad = dN @ Ginv.T  # row a: F^-T grad_xi N_a
-                ua = grad @ u
-                dV = w1 * w2 * w3 * det
-                A += dV * (np.outer(N, N) / dt + np.outer(N, ua) + kd * grad @ grad.T + sr * np.outer(N, N)
-                           + tau * np.outer(ua, N / dt + ua + sr * N))
-                b += dV * (N + tau * ua) * (N @ phi) / dt
+    for w, N, dN in pts:
+        grad = dN @ Ginv.T  # row a: F^-T grad_xi N_a
+        ua = grad @ u
+        dV = w * det
+        A += dV * (np.outer(N, N) / dt + np.outer(N, ua) + kd * grad @ grad.T + sr * np.outer(N, N)
+                   + tau * np.outer(ua, N / dt + ua + sr * N))
+        b += dV * (N + tau * ua) * (N @ phi) / dt
     Ao, bo = element_terms(t, xe, np.tile(u, (nen, 1)), kd, sr, phi, dt, O.ALL_TERMS)
     assert np.abs(Ao - A).max() <= 1e-12 * np.abs(A).max()
     assert np.abs(bo - b).max() <= 1e-12 * np.abs(b).max()
 
 
-@pytest.mark.parametrize("t", (O.HEX8, O.HEX27))
-def test_affine_hex_matches_high_order_rule(t):
-    check_affine_hex_high_order(t)
+@pytest.mark.parametrize("t", TYPES)
+def test_affine_element_matches_high_order_rule(t):
+    check_affine_high_order(t)
 
 
 def test_prism_closed_forms():
@@ -775,7 +829,7 @@ def all_pins():
     pins += [lambda: check_box_closed_forms(O.HEX8), lambda: check_box_closed_forms(O.HEX27),
              lambda: check_tet_closed_forms(np.random.default_rng(7)), check_pattern_counts,
              lambda: check_bruteforce(O.HEX8), check_mixed, check_prism_closed_forms,
-             lambda: check_affine_hex_high_order(O.HEX8), lambda: check_affine_hex_high_order(O.HEX27)]
+             *[lambda t=t: check_affine_high_order(t) for t in TYPES]]
     try:
         import sympy  # noqa: F401  (the pyramid's exact integrals)
         pins.append(check_pyramid_closed_forms)
