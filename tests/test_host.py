@@ -187,3 +187,15 @@ def test_profiled_traffic_goes_null_when_the_kernels_change(tmp_path, monkeypatc
     with open(csrc / "fea_api.cu", "a") as f:
         f.write("\n")
     assert bench.kernel_source_digest() != digest and bench.profiled_traffic("w") is None
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without the built CUDA library every call raises; there is no CPU fallback."""
+    monkeypatch.setattr(fea, "_lib", None)
+    missing = str(tmp_path / "libfea.so")
+    with pytest.raises(FileNotFoundError, match="missing"):
+        fea.lib(missing)
+    monkeypatch.setattr(fea, "LIB_PATH", missing)
+    monkeypatch.setattr(fea.lib, "__defaults__", (missing,))
+    with pytest.raises(FileNotFoundError):
+        fea.fea_version()
