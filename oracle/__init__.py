@@ -26,7 +26,11 @@ NEN = {TET4: 4, HEX8: 8, HEX27: 27, PEN6: 6, PYR5: 5}
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fea_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "_build", "libfea_oracle.so")
+# a second build with the planted mistakes compiled in (-DOR_MUTATION), loaded only by
+# ``mutation()``; the oracle proper has none of them
+_MUT_PATH = os.path.join(_HERE, "_build", "libfea_oracle_mut.so")
 _lib = None
+_mut_lib = None
 _lock = threading.Lock()
 
 _d = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
@@ -37,41 +41,51 @@ _I = C.c_int
 _D = C.c_double
 
 
+def _compile(path: str, extra, force: bool) -> str:
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        tmp = path + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (gcc, -O2, no FP contraction)."""
-    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return _compile(_LIB_PATH, [], force)
+
+
+def build_mutant(force: bool = False) -> str:
+    """Compile the test-only build that carries the planted mistakes (``mutation()``)."""
+    return _compile(_MUT_PATH, ["-DOR_MUTATION"], force)
+
+
+def _declare(L):
+    L.or_shape.argtypes = [_I, _d, _d, _d]
+    L.or_quadrature.argtypes = [_I, _d, _d]
+    L.or_element.argtypes = [_I, _d, _d, _d, _d, _d, _D, _I, _d, _d]
+    L.or_validate.argtypes = [_I, _d, _L, _i32, _L]
+    L.or_incidence.argtypes = [_I, _i32, _L, _L, _i64, _i64]
+    L.or_pattern_rowptr.argtypes = [_I, _i32, _L, _L, _i64, _i64, _i64]
+    L.or_pattern_rowptr.restype = C.c_int64
+    L.or_pattern_colind.argtypes = [_I, _i32, _L, _i64, _i64, _i64, _i32]
+    L.or_posmap.argtypes = [_I, _i32, _L, _i64, _i32, _i32]
+    L.or_assemble.argtypes = [_I, _d, _L, _i32, _L, _L, _i64, _i32, _L, _d, _d, _d, _d, _D, _I, _I,
+                              _d, _d, C.c_void_p, C.c_void_p]
+    L.or_row.argtypes = [_I, _d, _L, _i32, _i64, _i64, _L, _d, _d, _d, _d, _D, _I, _I, _L, _i32, _d, _d,
+                         _d, _d]
+    L.or_row.restype = C.c_int64
+    L.or_apply.argtypes = [_I, _d, _L, _i32, _L, _d, _d, _d, _d, _D, _I, _I, _d, _d]
+    L.or_update_fields.argtypes = [_d, _L, _I, _d, _d]
+    return L
 
 
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = C.CDLL(path)
-            L.or_set_mutation.argtypes = [_I]
-            L.or_shape.argtypes = [_I, _d, _d, _d]
-            L.or_quadrature.argtypes = [_I, _d, _d]
-            L.or_element.argtypes = [_I, _d, _d, _d, _d, _d, _D, _I, _d, _d]
-            L.or_validate.argtypes = [_I, _d, _L, _i32, _L]
-            L.or_incidence.argtypes = [_I, _i32, _L, _L, _i64, _i64]
-            L.or_pattern_rowptr.argtypes = [_I, _i32, _L, _L, _i64, _i64, _i64]
-            L.or_pattern_rowptr.restype = C.c_int64
-            L.or_pattern_colind.argtypes = [_I, _i32, _L, _i64, _i64, _i64, _i32]
-            L.or_posmap.argtypes = [_I, _i32, _L, _i64, _i32, _i32]
-            L.or_assemble.argtypes = [_I, _d, _L, _i32, _L, _L, _i64, _i32, _L, _d, _d, _d, _d, _D, _I, _I,
-                                      _d, _d, C.c_void_p, C.c_void_p]
-            L.or_row.argtypes = [_I, _d, _L, _i32, _i64, _i64, _L, _d, _d, _d, _d, _D, _I, _I, _L, _i32, _d, _d,
-                                 _d, _d]
-            L.or_row.restype = C.c_int64
-            L.or_apply.argtypes = [_I, _d, _L, _i32, _L, _d, _d, _d, _d, _D, _I, _I, _d, _d]
-            L.or_update_fields.argtypes = [_d, _L, _I, _d, _d]
-            _lib = L
+            _lib = _declare(C.CDLL(build()))
     return _lib
 
 
@@ -85,13 +99,21 @@ def _c(conn) -> np.ndarray:
 
 @contextlib.contextmanager
 def mutation(m: int):
-    """Temporarily plant deliberate mistake ``m`` in the oracle (tests of the pins)."""
-    L = lib()
-    L.or_set_mutation(int(m))
+    """Temporarily route every call to the test-only build with deliberate mistake ``m``
+    switched on (tests of the pins)."""
+    global _lib, _mut_lib
+    with _lock:
+        if _mut_lib is None:
+            _mut_lib = _declare(C.CDLL(build_mutant()))
+            _mut_lib.or_set_mutation.argtypes = [_I]
+    good = lib()
+    _mut_lib.or_set_mutation(int(m))
+    _lib = _mut_lib
     try:
         yield
     finally:
-        L.or_set_mutation(0)
+        _mut_lib.or_set_mutation(0)
+        _lib = good
 
 
 def quadrature(elem_type: int):

@@ -50,11 +50,17 @@ enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_RANGE = 2, OR_ERR_DUP = 3, OR_ERR_INVER
 
 #define MAXN 27
 
-/* Deliberate-mistake switch used only by the tests that show the pins catch
- * plausible errors.  0 = the correct oracle. */
+/* Deliberate mistakes, for the tests that show the pins catch plausible errors.
+ * They exist only in a second, test-only build compiled with -DOR_MUTATION; in the
+ * oracle itself MUT(k) is the constant 0 and every planted branch compiles away. */
+#ifdef OR_MUTATION
 static int g_mutation = 0;
+#define MUT(k) (g_mutation == (k))
 void or_set_mutation(int m) { g_mutation = m; }
 int or_get_mutation(void) { return g_mutation; }
+#else
+#define MUT(k) 0
+#endif
 
 /* ---------------------------------------------------------------- reference elements */
 
@@ -64,7 +70,7 @@ static void lagrange1d(int order, int i, double t, double* val, double* der) {
   double nodes[3];
   int q = order + 1;
   for (int m = 0; m < q; ++m) nodes[m] = -1.0 + 2.0 * m / order;
-  if (g_mutation == 11 && order == 2) { double s = nodes[1]; nodes[1] = nodes[2]; nodes[2] = s; }
+  if (MUT(11) && order == 2) { double s = nodes[1]; nodes[1] = nodes[2]; nodes[2] = s; }
   double v = 1.0;
   for (int m = 0; m < q; ++m)
     if (m != i) v *= (t - nodes[m]) / (nodes[i] - nodes[m]);
@@ -100,7 +106,7 @@ int or_shape(int type, const double* xi, double* N, double* dN) {
     /* prism: linear triangle in (xi, eta) times linear in zeta on [-1, 1]; node i + 3k is
      * triangle vertex i ((0,0), (1,0), (0,1)) on the face zeta = -1 (k = 0) or +1 (k = 1) */
     double L[3] = {1.0 - xi[0] - xi[1], xi[0], xi[1]};
-    if (g_mutation == 13) { double t = L[0]; L[0] = L[1]; L[1] = t; }
+    if (MUT(13)) { double t = L[0]; L[0] = L[1]; L[1] = t; }
     const double dLx[3] = {-1.0, 1.0, 0.0}, dLy[3] = {-1.0, 0.0, 1.0};
     const double l[2] = {0.5 * (1.0 - xi[2]), 0.5 * (1.0 + xi[2])}, dl[2] = {-0.5, 0.5};
     for (int k = 0; k < 2; ++k)
@@ -160,7 +166,7 @@ int or_quadrature(int type, double* xi, double* w) {
       xi[g * 3 + 0] = lam[1];
       xi[g * 3 + 1] = lam[2];
       xi[g * 3 + 2] = lam[3];
-      w[g] = (g_mutation == 5) ? 1.0 / 6.0 : 1.0 / 24.0;
+      w[g] = (MUT(5)) ? 1.0 / 6.0 : 1.0 / 24.0;
     }
     return 4;
   }
@@ -193,7 +199,7 @@ int or_quadrature(int type, double* xi, double* w) {
           xi[g * 3 + 0] = rp[i] * c;
           xi[g * 3 + 1] = rp[j] * c;
           xi[g * 3 + 2] = z;
-          w[g] = 0.5 * zw[k] * (g_mutation == 12 ? 1.0 : c * c);
+          w[g] = 0.5 * zw[k] * (MUT(12) ? 1.0 : c * c);
         }
     return 12;
   }
@@ -313,7 +319,7 @@ static int element_impl(int type, const double* xe, const double* ue, const doub
       for (int i = 0; i < 3; ++i) {
         double s = 0.0;
         for (int j = 0; j < 3; ++j)
-          s += (g_mutation == 4 ? Ji[i][j] : Ji[j][i]) * dNr[g][a * 3 + j];
+          s += (MUT(4) ? Ji[i][j] : Ji[j][i]) * dNr[g][a * 3 + j];
         gradN[g][a][i] = s;
       }
     dV[g] = wq[g] * det;
@@ -346,14 +352,14 @@ static int element_impl(int type, const double* xe, const double* ue, const doub
     if (terms & OR_MASS)
       for (int a = 0; a < nen; ++a)
         for (int b = 0; b < nen; ++b)
-          Ae[a * nen + b] += w * Ng[a] * (g_mutation == 10 ? Ng[a] : Ng[b]) / dt;
+          Ae[a * nen + b] += w * Ng[a] * (MUT(10) ? Ng[a] : Ng[b]) / dt;
     if (terms & OR_CONV)
       for (int a = 0; a < nen; ++a)
         for (int b = 0; b < nen; ++b) {
-          double c = (g_mutation == 3) ? Ng[b] * ua[a] : Ng[a] * ua[b];
-          Ae[a * nen + b] += (g_mutation == 2 ? -w : w) * c;
+          double c = (MUT(3)) ? Ng[b] * ua[a] : Ng[a] * ua[b];
+          Ae[a * nen + b] += (MUT(2) ? -w : w) * c;
         }
-    if ((terms & OR_DIFF) && g_mutation != 1)
+    if ((terms & OR_DIFF) && !MUT(1))
       for (int a = 0; a < nen; ++a)
         for (int b = 0; b < nen; ++b)
           Ae[a * nen + b] += w * kg *
@@ -365,16 +371,16 @@ static int element_impl(int type, const double* xe, const double* ue, const doub
     if (terms & OR_SUPG)
       for (int a = 0; a < nen; ++a)
         for (int b = 0; b < nen; ++b) {
-          double resid = Ng[b] / dt + ua[b] + (g_mutation == 7 ? 0.0 : sg * Ng[b]);
+          double resid = Ng[b] / dt + ua[b] + (MUT(7) ? 0.0 : sg * Ng[b]);
           Ae[a * nen + b] += w * tau * ua[a] * resid;
         }
     if (terms & OR_MASS)
       for (int a = 0; a < nen; ++a) be[a] += w * Ng[a] * pg / dt;
-    if ((terms & OR_SUPG) && g_mutation != 6)
+    if ((terms & OR_SUPG) && !MUT(6))
       for (int a = 0; a < nen; ++a) be[a] += w * tau * ua[a] * pg / dt;
     if (babs)
       for (int a = 0; a < nen; ++a) {
-        if (terms & OR_MASS) babs[a] += fabs(w * Ng[a] * pg / dt);
+        if (terms & OR_MASS) babs[a] += MUT(16) ? w * Ng[a] * pg / dt : fabs(w * Ng[a] * pg / dt);
         if (terms & OR_SUPG) babs[a] += fabs(w * tau * ua[a] * pg / dt);
       }
   }
@@ -471,7 +477,7 @@ static int64_t row_columns(int nen, const int32_t* conn, const int64_t* inc_ptr,
   int64_t u = 0;
   for (int64_t i = 0; i < c; ++i)
     if (i == 0 || buf[i] != buf[u - 1]) buf[u++] = buf[i];
-  if (g_mutation == 8) { /* drop the diagonal */
+  if (MUT(8)) { /* drop the diagonal */
     int64_t v = 0;
     for (int64_t i = 0; i < u; ++i)
       if (buf[i] != r) buf[v++] = buf[i];
@@ -565,11 +571,11 @@ int or_assemble(int type, const double* coords, int64_t n_node, const int32_t* c
       for (int a = 0; a < nen; ++a) {
         for (int b = 0; b < nen; ++b) {
           int32_t r = ce[a], c = ce[b];
-          if (g_mutation == 9) { r = ce[b]; c = ce[a]; }
+          if (MUT(9)) { r = ce[b]; c = ce[a]; }
           int64_t k = find_col(rowptr, colind, r, c);
           if (k < 0) return OR_ERR_ARG;
           values[(int64_t)q * nnz + k] += Ae[a * nen + b];
-          if (absA) absA[(int64_t)q * nnz + k] += fabs(Ae[a * nen + b]);
+          if (absA) absA[(int64_t)q * nnz + k] += MUT(17) ? Ae[a * nen + b] : fabs(Ae[a * nen + b]);
         }
         rhs[(int64_t)q * n_node + ce[a]] += be[a];
         if (absb) absb[(int64_t)q * n_node + ce[a]] += bab[a];
@@ -598,11 +604,12 @@ int64_t or_row(int type, const double* coords, int64_t n_node, const int32_t* co
     absr[q] = 0.0;
   }
   double xe[MAXN * 3], ue[MAXN * 3], ke[MAXN], se[MAXN], pe[MAXN], Ae[MAXN * MAXN], be[MAXN], bab[MAXN];
-  for (int64_t t = inc_ptr[r]; t < inc_ptr[r + 1]; ++t) {
+  for (int64_t t = inc_ptr[r]; t < inc_ptr[r + 1] - (MUT(15) ? 1 : 0); ++t) {
     int64_t e = inc_elem[t];
     const int32_t* ce = conn + e * nen;
     int a = 0;
     while (ce[a] != r) ++a;
+    if (MUT(14)) a = (a + 1) % nen;
     for (int q = 0; q < n_eq; ++q) {
       gather(nen, ce, coords, n_node, vel, kd, sr, phi, q, xe, ue, ke, se, pe);
       int st = element_impl(type, xe, ue, ke, se, pe, dt, terms, Ae, be, bab);

@@ -819,6 +819,162 @@ def test_solve_recovers_a_chosen_solution():
 
 # ------------------------------------------------------------------ planted mistakes
 
+# ------------------------------------------------------------------ sampled rows and abs-sum denominators
+
+def _fields_two_eq(rng, mesh, signed_phi=False):
+    N = mesh.n_node
+    lo = -1.0 if signed_phi else 0.0
+    return G.Fields(G.velocity_field(mesh.coords), rng.uniform(0.01, 0.1, (2, N)), rng.uniform(0, 5, (2, N)),
+                    rng.uniform(lo, 1, (2, N)), 1e-3)
+
+
+def check_row_sampler(t):
+    """RowSampler (the oracle's row-by-row path, ``or_row``: its own column list, local-index
+    search and accumulation) gives every row of the whole-mesh assembly ``or_assemble`` (itself
+    pinned by the checks above): the same columns, values, abs-sum denominators, RHS entry and
+    RHS denominator, for two equations.  Node and element ids are permuted, so neither the local
+    index of a row's node nor the order of its incident elements is the natural one (Sec. 4.2:
+    the CSR rows both paths build)."""
+    n, frac = INV_MESH[t]
+    mesh = small_mesh(t, n, frac, seed=17)
+    rng = np.random.default_rng(23)
+    G.permute_nodes(mesh, rng.permutation(mesh.n_node).astype(np.int64))
+    G.permute_elements(mesh, rng.permutation(mesh.n_elem).astype(np.int64))
+    f = _fields_two_eq(rng, mesh, signed_phi=True)
+    rp, ci, _ = O.pattern(t, mesh.conn, mesh.n_node, with_pos=False)
+    vals, rhs, absA, absb = O.assemble(t, mesh.coords, mesh.conn, rp, ci, f, with_abs=True)
+    rs = O.RowSampler(t, mesh.coords, mesh.conn, f)
+    for r in range(mesh.n_node):
+        cols, v, av, b, ab = rs.row(r)
+        k0, k1 = rp[r], rp[r + 1]
+        assert np.array_equal(cols, ci[k0:k1])
+        for got, want in ((v, vals[:, k0:k1]), (av, absA[:, k0:k1]), (b, rhs[:, r]), (ab, absb[:, r])):
+            assert np.abs(got - want).max() <= 1e-15 * np.abs(want).max()
+
+
+def check_row_sampler_mixed():
+    """On a mesh of Hex8, Pyr5 and Pen6 blocks, the rows RowSampler gives for each block, added
+    into the union pattern, are the rows of the whole-mesh assembly of all blocks."""
+    mm = G.mixed_mesh(3)
+    G.perturb_interior(mm, np.random.default_rng(31), 0.1)
+    N = mm.n_node
+    rng = np.random.default_rng(32)
+    f = G.Fields(G.velocity_field(mm.coords), rng.uniform(0.01, 0.1, (2, N)), rng.uniform(0, 5, (2, N)),
+                 rng.uniform(-1, 1, (2, N)), 1e-3)
+    rp, ci, _ = O.pattern_mixed(mm.blocks, N, with_pos=False)
+    vals, rhs, absA, absb = O.assemble_mixed(mm.coords, mm.blocks, rp, ci, f, with_abs=True)
+    samplers = [O.RowSampler(t, mm.coords, conn, f) for t, conn in mm.blocks]
+    for r in range(N):
+        k0, k1 = rp[r], rp[r + 1]
+        v = np.zeros((2, k1 - k0))
+        av = np.zeros_like(v)
+        b = np.zeros(2)
+        ab = np.zeros(2)
+        for rs in samplers:
+            cols, bv, bav, bb, bab = rs.row(r)
+            idx = np.searchsorted(ci[k0:k1], cols)
+            assert np.array_equal(ci[k0:k1][idx], cols)
+            v[:, idx] += bv
+            av[:, idx] += bav
+            b += bb
+            ab += bab
+        for got, want in ((v, vals[:, k0:k1]), (av, absA[:, k0:k1]), (b, rhs[:, r]), (ab, absb[:, r])):
+            assert np.abs(got - want).max() <= 1e-14 * np.abs(want).max()
+
+
+def check_abs_sums(t):
+    """The abs-sum denominators of the parity tolerances: absA_ij = sum_e |A^e_ij| (the element
+    matrices scattered densely by numpy, in magnitude), and absA >= |A|, absb >= |b| everywhere."""
+    n, frac = INV_MESH[t]
+    mesh = small_mesh(t, n, frac, seed=19)
+    rng = np.random.default_rng(29)
+    f = _fields_two_eq(rng, mesh, signed_phi=True)
+    N = mesh.n_node
+    rp, ci, _ = O.pattern(t, mesh.conn, N, with_pos=False)
+    vals, rhs, absA, absb = O.assemble(t, mesh.coords, mesh.conn, rp, ci, f, with_abs=True)
+    assert np.all(absA >= np.abs(vals)) and np.all(absb >= np.abs(rhs))
+    assert np.any(absb > 1.5 * np.abs(rhs))  # signed fields: some RHS entries do cancel
+    for q in range(2):
+        dense = np.zeros((N, N))
+        for e in mesh.conn:
+            Ae, _ = O.element(t, mesh.coords[e], f.velocity[:, e].T, f.diffusivity[q, e], f.reaction[q, e],
+                              f.phi_old[q, e], f.dt)
+            dense[np.ix_(e, e)] += np.abs(Ae)
+        got = sp.csr_matrix((absA[q], ci, rp), shape=(N, N)).toarray()
+        assert np.abs(got - dense).max() <= 1e-13 * dense.max()
+
+
+TET_BARY_A, TET_BARY_B = 0.5854101966249685, 0.1381966011250105
+
+
+def check_abs_rhs_by_hand():
+    """absb on two tetrahedra, summed by hand: for every element, Gauss point and node, the
+    magnitudes of the Galerkin summand dV N_a phi_g/dt and of the SUPG summand
+    dV tau (u_g.grad N_a) phi_g/dt.  The P1 gradients come from inverting the 4 x 4 matrix of
+    barycentric coordinates, the points are the (a, b, b, b) barycentric points with dV = V/4,
+    tau = 1/(4k/h^2 + 2|u|/h + s) with h = V^(1/3).  phi changes sign inside each element, so
+    the summands of one node do have both signs (the sum of magnitudes exceeds |b|)."""
+    coords = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1.2]], float)
+    conn = np.array([[0, 1, 2, 3], [1, 2, 3, 4]], np.int32)
+    # the second tet: make it positively oriented
+    x = coords[conn[1]]
+    if np.dot(np.cross(x[1] - x[0], x[2] - x[0]), x[3] - x[0]) < 0:
+        conn[1] = conn[1][[0, 2, 1, 3]]
+    N = coords.shape[0]
+    vel = np.array([[0.3, -0.2, 0.5, 0.1, 0.4], [0.1, 0.6, -0.3, 0.2, 0.0], [0.2, 0.2, 0.2, -0.5, 0.3]])
+    k = np.array([[0.02, 0.05, 0.03, 0.04, 0.01]])
+    s = np.array([[1.0, 2.0, 0.5, 3.0, 1.5]])
+    phi = np.array([[1.0, -0.8, 0.6, -1.1, 0.9]])
+    dt = 1e-2
+    f = G.Fields(vel, k, s, phi, dt)
+    rp, ci, _ = O.pattern(O.TET4, conn, N, with_pos=False)
+    _, rhs, _, absb = O.assemble(O.TET4, coords, conn, rp, ci, f, with_abs=True)
+    want_b = np.zeros(N)
+    want_abs = np.zeros(N)
+    signs = set()
+    for e in conn:
+        X = coords[e]
+        M = np.hstack([np.ones((4, 1)), X])
+        V = abs(np.linalg.det(M)) / 6.0
+        grad = np.linalg.inv(M)[1:, :].T          # row a = grad of barycentric coordinate a
+        h = V ** (1.0 / 3.0)
+        for g in range(4):
+            lam = np.full(4, TET_BARY_B)
+            lam[g] = TET_BARY_A
+            ug = vel[:, e] @ lam
+            kg, sg, pg = k[0, e] @ lam, s[0, e] @ lam, phi[0, e] @ lam
+            tau = 1.0 / (4 * kg / h ** 2 + 2 * np.linalg.norm(ug) / h + sg)
+            dV = V / 4.0
+            for a in range(4):
+                gal = dV * lam[a] * pg / dt
+                supg = dV * tau * (ug @ grad[a]) * pg / dt
+                want_b[e[a]] += gal + supg
+                want_abs[e[a]] += abs(gal) + abs(supg)
+                signs.add((int(e[a]), np.sign(gal)))
+    assert any((n, 1.0) in signs and (n, -1.0) in signs for n in range(N))
+    assert np.any(want_abs > 1.2 * np.abs(want_b))
+    assert np.allclose(rhs[0], want_b, rtol=1e-13, atol=0)
+    assert np.allclose(absb[0], want_abs, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("t", TYPES)
+def test_row_sampler_equals_assembly(t):
+    check_row_sampler(t)
+
+
+def test_row_sampler_mixed_mesh():
+    check_row_sampler_mixed()
+
+
+@pytest.mark.parametrize("t", TYPES)
+def test_abs_sum_denominators(t):
+    check_abs_sums(t)
+
+
+def test_abs_rhs_summed_by_hand():
+    check_abs_rhs_by_hand()
+
+
 def all_pins():
     rng = np.random.default_rng(1)
     pins = []
@@ -829,7 +985,9 @@ def all_pins():
     pins += [lambda: check_box_closed_forms(O.HEX8), lambda: check_box_closed_forms(O.HEX27),
              lambda: check_tet_closed_forms(np.random.default_rng(7)), check_pattern_counts,
              lambda: check_bruteforce(O.HEX8), check_mixed, check_prism_closed_forms,
-             *[lambda t=t: check_affine_high_order(t) for t in TYPES]]
+             *[lambda t=t: check_affine_high_order(t) for t in TYPES],
+             *[lambda t=t: check_row_sampler(t) for t in TYPES], check_row_sampler_mixed,
+             *[lambda t=t: check_abs_sums(t) for t in TYPES], check_abs_rhs_by_hand]
     try:
         import sympy  # noqa: F401  (the pyramid's exact integrals)
         pins.append(check_pyramid_closed_forms)
@@ -877,6 +1035,10 @@ MUTATIONS = {
     11: "quadratic 1-D nodes in the wrong order",
     12: "pyramid rule without the collapse factor (1 - zeta)^2",
     13: "prism triangle functions permuted, derivatives not",
+    14: "sampled row uses the wrong local index of its node",
+    15: "sampled row skips an incident element",
+    16: "RHS denominator sums the Galerkin summands with their signs",
+    17: "matrix denominator sums the element entries with their signs",
 }
 
 
