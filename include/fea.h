@@ -123,7 +123,11 @@ typedef struct {
                                autotuned count under FEA_SCATTER_AUTO */
   int32_t cancel_check;     /* FP32 path: 1 = rows whose sums cancel are redone in FP64 (see
                                fea_cancel_rows); not allowed with accumulate.  Default 0 */
-  int32_t reserved[2];
+  int32_t host_parts;       /* fea_assemble_host only: the equations are assembled in this many parts,
+                               each part's values copied back while the next part computes (at most
+                               n_eq); 0 = automatic: 3 when the values exceed 256 MB and n_eq >= 3,
+                               else 1.  Default 0 */
+  int32_t reserved[1];
 } fea_assemble_opts;
 
 /* Fills *opts with the defaults listed above. */
@@ -250,8 +254,10 @@ FEA_API fea_status fea_pack_plan(const int64_t* count_by_type, int32_t n_types, 
  * one fixed 128 KiB array per GPU that every call in the process shares; each call rewrites
  * the part it uses, so nothing has to be cleared, but calls whose work overlaps on the GPU
  * (other streams, other threads) race on that array and must be serialised by the caller.
- * The first call on each GPU looks up the array's device address with that GPU current;
- * make that first call before any stream capture.
+ * The first call on each GPU looks up the array's device address with that GPU current and
+ * keeps it for the life of the process; make that first call before any stream capture, and
+ * do not call this function again on a GPU after cudaDeviceReset in the same process (the
+ * kept address would belong to the destroyed context).
  */
 FEA_API fea_status fea_csr_rowptr_noalloc(const int32_t* counts, int64_t n, int64_t* rowptr, void* stream);
 
@@ -326,11 +332,15 @@ FEA_API fea_status fea_tuned_strategy(const fea_pattern* pattern, int32_t n_eq, 
  * fea_cancel_rows -- the cancellation check (opts.cancel_check = 1, FP32 path).  Row i of an
  * equation is flagged when an entry with |A_ij| > 1e-3 max_j |A_ij| has
  * sum_e |A^e_ij| > 1e3 |A_ij|, or when sum_e |b^e_i| > 1e3 |b_i| (the sums over the elements
- * containing the row's node).  The first checked assembly for a pattern and n_eq computes the
- * flags in one FP32 pass over all rows (it waits for the GPU; it cannot run under stream
- * capture) and keeps them while the pattern lives; every checked assembly then recomputes the
- * flagged rows, element rows formed and summed in FP64 from the same inputs, after the main
- * assembly.  *count = number of flagged rows; FEA_ERR_STATE before the first checked call.
+ * containing the row's node); a row is flagged if any equation flags it.  Every checked
+ * assembly computes the flags from its own inputs, in one FP32 pass over all rows, then
+ * recomputes the flagged rows after the main assembly: element rows formed and summed in FP64
+ * from the same inputs, rounded into the outputs.  The check is device work on the mesh's
+ * stream, with no host wait, so checked assemblies can be recorded in a step graph; the first
+ * checked assembly for a pattern and n_eq allocates the check's buffers and must come before
+ * any stream capture.  The flag pass costs several times the element work of the assembly.
+ * *count = the number of rows the most recent checked assembly for this n_eq flagged (the call
+ * waits for the mesh's stream); FEA_ERR_STATE before the first checked call.
  */
 FEA_API fea_status fea_cancel_rows(const fea_pattern* pattern, int32_t n_eq, int64_t* count);
 

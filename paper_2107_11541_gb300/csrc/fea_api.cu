@@ -375,6 +375,7 @@ static fea_status check_assemble_args(fea_mesh* m, const fea_pattern* p, const v
     return fail(FEA_ERR_ARG, "the gather scatter is an FP32 path");
   if (o->cancel_check != 0 && o->cancel_check != 1) return fail(FEA_ERR_ARG, "cancel_check must be 0 or 1");
   if (o->cancel_check && o->accumulate) return fail(FEA_ERR_ARG, "cancel_check cannot be combined with accumulate");
+  if (o->host_parts < 0) return fail(FEA_ERR_ARG, "host_parts must be >= 0");
   if (m->mixed && (o->scatter == FEA_SCATTER_ROWOWNED || o->scatter == FEA_SCATTER_GATHER || o->cancel_check))
     return fail(FEA_ERR_ARG, "a mesh of several element types scatters with atomics (no row-owned, gather or "
                              "cancellation check)");
@@ -838,7 +839,11 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->pcg_ws);
   cudaFree(p->elem_order);
   cudaFree(p->hex8_fnode);
-  for (auto& kv : p->cancel) cudaFree(kv.second.first);
+  for (auto& kv : p->cancel) {
+    cudaFree(kv.second.rows);
+    cudaFree(kv.second.count);
+  }
+  cudaFree(p->cancel_flags);
   plan_destroy(p->plan);
   delete p;
   return FEA_OK;
@@ -962,15 +967,23 @@ fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, cons
   FEA_TRY(run_strategy(m, pw, vel, kd, sr, phi, dt, n_eq, om, values, rhs, st));
   AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
   auto it = pw->cancel.find(n_eq);
-  if (it == pw->cancel.end()) {
+  if (it == pw->cancel.end()) {  // the flag and row buffers: allocated once, before any capture
     if (stream_capturing(m->stream))
-      return fail(FEA_ERR_STATE, "the cancellation flags must be computed by a checked call before stream capture");
-    int32_t* rows = nullptr;
-    int64_t count = 0;
-    FEA_TRY(cancel_flag_rows(a, m->type, p->maxcol, &rows, &count, m->stream));
-    it = pw->cancel.emplace(n_eq, std::make_pair(rows, count)).first;
+      return fail(FEA_ERR_STATE, "the first checked assembly for an equation count allocates the cancellation "
+                                 "buffers and cannot run under stream capture");
+    const size_t n = (size_t)std::max<int64_t>(m->n_node, 1);
+    fea_pattern::CancelRows cr{nullptr, nullptr};
+    if ((!pw->cancel_flags && cudaMalloc(&pw->cancel_flags, n) != cudaSuccess) ||
+        cudaMalloc(&cr.rows, sizeof(int32_t) * n) != cudaSuccess ||
+        cudaMalloc(&cr.count, sizeof *cr.count) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(cr.rows);
+      return fail(FEA_ERR_OOM, "cancellation check: device allocation failed");
+    }
+    FEA_CUDA_TRY(cudaMemsetAsync(cr.count, 0, sizeof *cr.count, m->stream));
+    it = pw->cancel.emplace(n_eq, cr).first;
   }
-  FEA_TRY(cancel_fix_rows(a, m->type, p->maxcol, it->second.first, it->second.second, m->stream));
+  FEA_TRY(cancel_check_rows(a, m->type, p->maxcol, pw->cancel_flags, it->second.rows, it->second.count, m->stream));
   if (o.event_end) FEA_CUDA_TRY(cudaEventRecord((cudaEvent_t)o.event_end, m->stream));
   return FEA_OK;
 }
@@ -1008,7 +1021,10 @@ fea_status fea_cancel_rows(const fea_pattern* p, int32_t n_eq, int64_t* count) {
   if (!p || !count) return fail(FEA_ERR_ARG, "fea_cancel_rows: null argument");
   auto it = p->cancel.find(n_eq);
   if (it == p->cancel.end()) return fail(FEA_ERR_STATE, "no checked assembly for %d equations yet", n_eq);
-  *count = it->second.second;
+  unsigned long long c = 0;
+  FEA_CUDA_TRY(cudaStreamSynchronize(p->mesh->stream));
+  FEA_CUDA_TRY(cudaMemcpy(&c, it->second.count, sizeof c, cudaMemcpyDeviceToHost));
+  *count = (int64_t)c;
   return FEA_OK;
 }
 
@@ -1096,7 +1112,8 @@ fea_status fea_assemble_host(fea_mesh* m, const fea_pattern* cp, const void* vel
   FEA_TRY(run_copies(in, n_in, cudaMemcpyHostToDevice, true));
   // Large outputs: the equations are assembled in parts, each an independent assembly of its
   // slices, so that part k's values travel back while part k+1 computes.
-  const int parts = (b_val > ((size_t)256 << 20) && n_eq >= 3) ? 3 : 1;  // 3 measured best of 3 and 6
+  const int parts = o.host_parts > 0 ? std::min(o.host_parts, n_eq)
+                                      : (b_val > ((size_t)256 << 20) && n_eq >= 3) ? 3 : 1;  // 3: best of 3 and 6
   const int per = (n_eq + parts - 1) / parts;
   for (int q0 = 0; q0 < n_eq; q0 += per) {
     const int cnt = std::min(per, n_eq - q0);

@@ -2,18 +2,21 @@
 // element contributions get their sums redone in FP64.
 //
 // A row i of equation q is flagged when, over its entries with |A_ij| > 1e-3 max_j |A_ij|,
-// some entry has sum_e |A^e_ij| / |A_ij| > 1e3, or when sum_e |b^e_i| / |b_i| > 1e3.  The
-// flags come from one FP32 pass over every row (the first checked assembly for a pattern
-// and equation count) and are kept while the mesh is unchanged; a row is flagged if any
-// equation flags it.  Every checked assembly then recomputes the flagged rows after the
-// main assembly: each incident element's row is formed and summed in FP64 from the same
-// (FP32) inputs, and the rounded sums overwrite the row.
+// some entry has sum_e |A^e_ij| / |A_ij| > 1e3, or when sum_e |b^e_i| / |b_i| > 1e3.  Every
+// checked assembly computes the flags afresh from its own inputs, in one FP32 pass over every
+// row (a row is flagged if any equation flags it), so that rows that start to cancel when the
+// fields change (a new time step, new properties) are caught.  The flagged rows are then
+// recomputed after the main assembly: each incident element's row is formed and summed in
+// FP64 from the same (FP32) inputs, and the rounded sums overwrite the row.  All of it is
+// stream-ordered device work: the FP64 pass reads the number of flagged rows from device
+// memory, so a checked assembly can be recorded in a CUDA graph.
 //
 // Both passes are row-centric: one warp per row walks the row's incident elements in
 // ascending order, computes each element's geometry and the row of its element matrix
 // (the per-warp element code of the element-parallel kernel) and adds it into the row's
 // accumulators in shared memory.  An element is recomputed once per node it owns in the
-// pass, which is affordable for one setup pass and for the few flagged rows.
+// pass: the flag pass costs several times the element work of the assembly itself, which is
+// why the check is an option; the FP64 pass touches only the few flagged rows.
 #include <algorithm>
 
 #include "fea_generic_elem.cuh"
@@ -27,7 +30,8 @@ constexpr float CANCEL_ENTRY_CUTOFF = 1e-3f;
 struct RowArgs {
   AsmArgs<float> a;
   const int32_t* rows;  // FIX: the flagged rows; FLAG: null (all rows)
-  int64_t n_rows;
+  int64_t n_rows;       // FLAG: rows to walk
+  const unsigned long long* n_rows_dev;  // FIX: the number of flagged rows, read on the device
   uint8_t* flags;       // FLAG: [n_node] output
   int acc_stride;       // maxcol + 1 (the RHS is column maxcol)
   int warps;
@@ -51,8 +55,9 @@ __global__ void k_rows_recompute(RowArgs r) {
   fill_shape_table<TC, TYPE>(Nt);
   __syncthreads();
   const TC inv_dt = TC(1.0 / p.dt);
+  const int64_t n_rows = MODE == MODE_FIX ? (int64_t)*r.n_rows_dev : r.n_rows;
 
-  for (int64_t i = (int64_t)blockIdx.x * r.warps + w; i < r.n_rows; i += (int64_t)gridDim.x * r.warps) {
+  for (int64_t i = (int64_t)blockIdx.x * r.warps + w; i < n_rows; i += (int64_t)gridDim.x * r.warps) {
     const int64_t row = MODE == MODE_FIX ? (int64_t)r.rows[i] : i;
     const int64_t k0 = p.rowptr[row];
     const int len = (int)(p.rowptr[row + 1] - k0);
@@ -135,8 +140,11 @@ fea_status launch_rows(const RowArgs& r0, cudaStream_t s) {
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int per_sm = 1;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+  // FLAG walks every row; FIX at most every row (its count is known only on the device), in
+  // one wave of CTAs that stride over the flagged rows
   const int64_t want = (r.n_rows + warps - 1) / warps;
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * std::max(per_sm, 1) * 8));
+  const int64_t cap = (int64_t)nsm * std::max(per_sm, 1) * (MODE == MODE_FLAG ? 8 : 1);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, cap));
   if (r.n_rows > 0) kern<<<grid, warps * 32, smem, s>>>(r);
   FEA_CUDA_TRY(cudaGetLastError());
   count_launches(1);
@@ -157,56 +165,26 @@ fea_status launch_rows_any(const RowArgs& r, fea_elem_t type, cudaStream_t s) {
 
 }  // namespace
 
-fea_status cancel_flag_rows(const AsmArgs<float>& a, fea_elem_t type, int maxcol, int32_t** rows, int64_t* count,
-                            cudaStream_t s) {
-  *rows = nullptr;
-  *count = 0;
+fea_status cancel_check_rows(const AsmArgs<float>& a, fea_elem_t type, int maxcol, uint8_t* flags, int32_t* rows,
+                             unsigned long long* count, cudaStream_t s) {
   const int64_t N = a.n_node;
-  uint8_t* flags = nullptr;
-  unsigned long long* dcount = nullptr;
-  int32_t* list = nullptr;
-  auto cleanup = [&](fea_status st) {
-    cudaFree(flags);
-    cudaFree(dcount);
-    if (st != FEA_OK) cudaFree(list);
-    return st;
-  };
-  if (cudaMalloc(&flags, std::max<int64_t>(N, 1)) != cudaSuccess || cudaMalloc(&dcount, sizeof *dcount) != cudaSuccess ||
-      cudaMalloc(&list, sizeof(int32_t) * std::max<int64_t>(N, 1)) != cudaSuccess) {
-    cudaGetLastError();
-    return cleanup(fail(FEA_ERR_OOM, "cancellation check: device allocation failed"));
-  }
+  if (N == 0) return FEA_OK;
   RowArgs r;
   r.a = a;
   r.rows = nullptr;
   r.n_rows = N;
+  r.n_rows_dev = nullptr;
   r.flags = flags;
   r.acc_stride = maxcol + 1;
   r.warps = 0;
-  fea_status st = launch_rows_any<float, MODE_FLAG>(r, type, s);
-  if (st != FEA_OK) return cleanup(st);
-  if (cudaMemsetAsync(dcount, 0, sizeof *dcount, s) != cudaSuccess) return cleanup(fail(FEA_ERR_CUDA, "memset failed"));
-  if (N > 0) k_compact_flags<<<(unsigned)std::min<int64_t>((N + 255) / 256, 152 * 8), 256, 0, s>>>(flags, N, list, dcount);
+  FEA_TRY((launch_rows_any<float, MODE_FLAG>(r, type, s)));
+  FEA_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof *count, s));
+  k_compact_flags<<<(unsigned)std::min<int64_t>((N + 255) / 256, 152 * 8), 256, 0, s>>>(flags, N, rows, count);
+  FEA_CUDA_TRY(cudaGetLastError());
   count_launches(1);
-  unsigned long long hc = 0;
-  if (cudaMemcpyAsync(&hc, dcount, sizeof hc, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    return cleanup(fail(FEA_ERR_CUDA, "cancellation check: %s", cudaGetErrorString(cudaGetLastError())));
-  *rows = list;
-  *count = (int64_t)hc;
-  return cleanup(FEA_OK);
-}
-
-fea_status cancel_fix_rows(const AsmArgs<float>& a, fea_elem_t type, int maxcol, const int32_t* rows, int64_t count,
-                           cudaStream_t s) {
-  if (count == 0) return FEA_OK;
-  RowArgs r;
-  r.a = a;
   r.rows = rows;
-  r.n_rows = count;
+  r.n_rows_dev = count;
   r.flags = nullptr;
-  r.acc_stride = maxcol + 1;
-  r.warps = 0;
   return launch_rows_any<double, MODE_FIX>(r, type, s);
 }
 

@@ -103,8 +103,15 @@ struct fea_pattern {
   size_t em_bytes;
   // autotuned strategy per equation count: {scatter, equation groups}
   std::map<int, std::pair<int, int>> tuned;
-  // cancellation check per equation count: {device list of flagged rows, count}
-  std::map<int, std::pair<int32_t*, int64_t>> cancel;
+  // cancellation check: the per-row flags every checked call recomputes ([n_node], shared by
+  // all equation counts), and per equation count the device list of the rows the most recent
+  // checked call flagged, with its device-side length
+  uint8_t* cancel_flags;
+  struct CancelRows {
+    int32_t* rows;                // [n_node]
+    unsigned long long* count;    // device
+  };
+  std::map<int, CancelRows> cancel;
   // device workspace for fea_assemble_host
   void* ws;
   size_t ws_bytes;
@@ -357,9 +364,10 @@ fea_status launch_gather_f32(const AsmArgs<float>& a, fea_elem_t type, int maxco
 size_t gather_scratch_bytes(int64_t n_elem, int nen, int n_eq);
 // Cancellation check: one FP32 pass flags rows (device list, owned by the caller afterwards,
 // and its length; waits for the GPU), and the FP64 recomputation of the listed rows.
-fea_status cancel_flag_rows(const AsmArgs<float>& a, fea_elem_t type, int maxcol, int32_t** rows, int64_t* count,
-                            cudaStream_t s);
-fea_status cancel_fix_rows(const AsmArgs<float>& a, fea_elem_t type, int maxcol, const int32_t* rows, int64_t count,
-                           cudaStream_t s);
+// The cancellation check of one assembly, all on the stream (no host wait, capturable): the FP32
+// flag pass over every row into flags[n_node], the flagged rows compacted into rows[] with their
+// number in *count, then those rows recomputed in FP64.
+fea_status cancel_check_rows(const AsmArgs<float>& a, fea_elem_t type, int maxcol, uint8_t* flags, int32_t* rows,
+                             unsigned long long* count, cudaStream_t s);
 
 }  // namespace fea

@@ -42,7 +42,8 @@ class FeaError(RuntimeError):
 class fea_assemble_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("terms", C.c_int32), ("scatter", C.c_int32), ("accumulate", C.c_int32),
                 ("kappa_threshold", C.c_double), ("event_begin", C.c_void_p), ("event_end", C.c_void_p),
-                ("eq_groups", C.c_int32), ("cancel_check", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("eq_groups", C.c_int32), ("cancel_check", C.c_int32), ("host_parts", C.c_int32),
+                ("reserved", C.c_int32 * 1)]
 
 
 _lib = None
