@@ -30,7 +30,8 @@ constexpr int MAX_DEVICES = 64;
 static std::mutex g_mu;
 static int64_t* g_scratch[MAX_DEVICES] = {nullptr};
 
-// Device address of g_tile_sums on the current device, looked up once per device.
+// Device address of g_tile_sums on the current device, looked up once per device and kept for
+// the life of the process (a cudaDeviceReset would invalidate it; the header says so).
 static fea_status scratch_address(int64_t** out) {
   int dev = 0;
   FEA_CUDA_TRY(cudaGetDevice(&dev));

@@ -171,7 +171,11 @@ def structured_mesh(elem_type: int, n: int, z_faces: np.ndarray | None = None) -
     elif elem_type == PYR5:
         cells = np.arange(n ** 3)
         conn = pyramid_conn(_cell_origins(n, m, 1), m, m ** 3 + cells)
-        coords = np.concatenate([coords, cell_centres(n, cells)])
+        centres = cell_centres(n, cells)
+        if z_faces is not None:  # the centre of each cell between its own z faces
+            k = cells // (n * n)
+            centres[:, 2] = 0.5 * (np.asarray(z_faces)[k] + np.asarray(z_faces)[k + 1])
+        coords = np.concatenate([coords, centres])
     else:
         conn = hex_conn(n, order)
     return Mesh(elem_type, coords, conn, n, 1.0 / n)
@@ -315,6 +319,21 @@ def make_workload(index: int, n: int | None = None, n_eq: int | None = None, see
         cfg["n"] = n
     if n_eq is not None:
         cfg["n_eq"] = n_eq
+    mesh, rng = _workload_mesh(index, cfg, seed, stretched_slab)
+    fields = draw_fields(rng, mesh.coords, cfg["n_eq"], cfg["s_max"])
+    return Workload(cfg["name"] if n is None and n_eq is None else f"{cfg['name']}_n{mesh.n_cells}_q{cfg['n_eq']}",
+                    mesh, fields, cfg["precision"])
+
+
+def make_mesh(index: int, n: int | None = None) -> Mesh:
+    """The mesh of workload ``index`` alone (the same draws as ``make_workload``, no fields)."""
+    cfg = dict(CONFIGS[index])
+    if n is not None:
+        cfg["n"] = n
+    return _workload_mesh(index, cfg, None, False)[0]
+
+
+def _workload_mesh(index: int, cfg: dict, seed: int | None, stretched_slab: bool):
     rng = np.random.default_rng(SEED_BASE + index if seed is None else seed)
     z_faces = None
     et, nc = cfg["elem_type"], cfg["n"]
@@ -340,9 +359,7 @@ def make_workload(index: int, n: int | None = None, n_eq: int | None = None, see
     if cfg["permute"]:
         permute_nodes(mesh, rng.permutation(mesh.n_node).astype(np.int64))
         permute_elements(mesh, rng.permutation(mesh.n_elem).astype(np.int64))
-    fields = draw_fields(rng, mesh.coords, cfg["n_eq"], cfg["s_max"])
-    return Workload(cfg["name"] if n is None and n_eq is None else f"{cfg['name']}_n{nc}_q{cfg['n_eq']}",
-                    mesh, fields, cfg["precision"])
+    return mesh, rng
 
 
 def single_element(elem_type: int, rng: np.random.Generator | None = None, distort: float = 0.0,

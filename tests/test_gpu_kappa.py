@@ -29,14 +29,16 @@ def rotated_slab(cfg, n, q):
     return w.mesh, w.fields
 
 
-def rotated_prism_slab(n, q):
-    """Prisms (triangles in the y-z planes) with the middle z layer 1e-4 as thick as the others."""
+def rotated_layer_slab(t, n, q):
+    """Elements of type t on an n^3 grid whose middle z layer of cells is 1e-4 as thick as the
+    others (prisms: triangles in the y-z planes; pyramids: six per cell around its centre;
+    tetrahedra: the Kuhn split), rotated off the axes."""
     widths = np.ones(n)
     widths[n // 2] = 1e-4
     widths /= widths.sum()
     faces = np.concatenate([[0.0], np.cumsum(widths)])
     faces[-1] = 1.0
-    mesh = G.structured_mesh(G.PEN6, n, faces)
+    mesh = G.structured_mesh(t, n, faces)
     fields = G.draw_fields(np.random.default_rng(12), mesh.coords, q, 50.0)
     mesh.coords = mesh.coords @ rotation().T
     return mesh, fields
@@ -71,7 +73,11 @@ def test_kappa_fallback_keeps_fp32_parity(cfg, n, q, scatter):
     check_fallback(mesh, fields, q, scatter)
 
 
-@pytest.mark.parametrize("scatter", [fea.FEA_SCATTER_ATOMIC, fea.FEA_SCATTER_GATHER], ids=["atomic", "gather"])
-def test_kappa_fallback_prisms(scatter):
-    mesh, fields = rotated_prism_slab(5, 2)
+@pytest.mark.parametrize("t,scatter", [(G.PEN6, fea.FEA_SCATTER_ATOMIC), (G.PEN6, fea.FEA_SCATTER_GATHER),
+                                       (G.TET4, fea.FEA_SCATTER_ATOMIC), (G.TET4, fea.FEA_SCATTER_GATHER),
+                                       (G.PYR5, fea.FEA_SCATTER_ATOMIC), (G.PYR5, fea.FEA_SCATTER_GATHER)],
+                         ids=["pen6_atomic", "pen6_gather", "tet4_atomic", "tet4_gather", "pyr5_atomic",
+                              "pyr5_gather"])
+def test_kappa_fallback_other_types(t, scatter):
+    mesh, fields = rotated_layer_slab(t, 5, 2)
     check_fallback(mesh, fields, 2, scatter)

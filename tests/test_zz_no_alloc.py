@@ -56,3 +56,19 @@ def test_noalloc_rowptr_edges():
     torch.cuda.synchronize()
     want = np.concatenate([[0], np.cumsum(counts.cpu().numpy().astype(np.int64))])
     assert np.array_equal(got.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("n", [5_000_001, 33_554_432], ids=["5M_rows", "max_rows"])
+def test_noalloc_rowptr_many_tiles(n):
+    """More than 2048 scan tiles (the tile-offset pass then carries over several rounds), up to
+    exactly the largest accepted size, against numpy's cumulative sum, twice in a row."""
+    import torch
+    rng = np.random.default_rng(n)
+    host = rng.integers(0, 130, size=n).astype(np.int32)
+    counts = torch.from_numpy(host).cuda()
+    want = np.concatenate([[0], np.cumsum(host.astype(np.int64))])
+    for _ in range(2):
+        got = torch.full((n + 1,), -1, dtype=torch.int64, device="cuda")
+        fea.fea_csr_rowptr_noalloc(counts, n, got)
+        torch.cuda.synchronize()
+        assert np.array_equal(got.cpu().numpy(), want)
