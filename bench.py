@@ -3,9 +3,12 @@
 
 One step = one fea_assemble call over the whole workload: gather, Gauss-point
 geometry, per-equation coefficients, element matrices and RHS, scatter into the
-CSR values and RHS of every equation.  Inputs are resident in HBM; the inputs
-plus outputs of every workload are larger than the 129 MB L2, so no L2 flush is
-needed between steps.
+CSR values and RHS of every equation.  On the default workload (Hex8 256^3, 32
+equations) a step is a time step: the assembly, then the seeded update of the
+field, K of them recorded in one CUDA graph.  Inputs are resident in HBM; the
+inputs plus outputs of every workload are larger than the 129 MB L2, so no L2
+flush is needed between steps.  The default run then measures the other
+paper-shaped workloads the same way ("workloads" in the output).
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 instead (a bounded sample of the same workload on the host cores).
@@ -32,14 +35,54 @@ WORKLOADS = {"tet4_100_perm_1eq": 1, "hex8_128_21eq": 2, "hex27_48_11eq": 3, "he
 # meshes of several element types (not among the paper-shaped configurations): cells per axis, equations
 MIXED_WORKLOADS = {"mixed_96_4eq": (96, 4)}
 NG = {G.TET4: 4, G.HEX8: 8, G.HEX27: 27, G.PEN6: 6, G.PYR5: 12}
-DEFAULT_WORKLOAD = "hex8_128_21eq"
+# the largest paper-shaped configuration that fits one GPU: Hex8 256^3, 32 equations, 10 time steps
+# in one CUDA graph; the default run also measures the other paper-shaped workloads (SIDE_WORKLOADS)
+DEFAULT_WORKLOAD = "hex8_256_32eq"
+SIDE_WORKLOADS = ("hex8_128_21eq", "hex27_48_11eq", "tet4_100_perm_1eq")
 METRIC = "elements x equations assembled per second (FP32 batched)"
 UNIT = "elem*eq/s"
 HBM_PEAK_FALLBACK = 6800.0
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ_FALLBACK = 2070.0
 NEN = {G.TET4: 4, G.HEX8: 8, G.HEX27: 27}
+
+
+def closed_form_nnz(workload: str, n=None) -> int:
+    """nnz of a paper-shaped workload's pattern by counting (pinned against the oracle's pattern by
+    the CPU tests): Kuhn tetrahedra of n^3 cubes have N + 2 x (edges) entries, edges = 3n(n+1)^2
+    axis edges + 3n^2(n+1) face diagonals + n^3 body diagonals; a tensor grid of Hex8 (Hex27)
+    elements has (3n+1)^3 ((8n+1)^3) entries, the cube of its 1-D row lengths."""
+    cfg = G.CONFIGS[WORKLOADS[workload]]
+    n, t = cfg["n"] if n is None else n, cfg["elem_type"]
+    if t == G.TET4:
+        return (n + 1) ** 3 + 2 * (3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3)
+    return (3 * n + 1) ** 3 if t == G.HEX8 else (8 * n + 1) ** 3
+
+
+def device_alu_peak():
+    """FP32 FMA peak of the current device in TFLOP/s: its SM count x 128 lanes x 2 flop x the
+    maximum SM clock (the measured one from MEASURED_PEAKS.json where present)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peaks = measured_peaks()
+    mhz = float(peaks.get("sm_max_mhz", SM_MAX_MHZ_FALLBACK)) if peaks else SM_MAX_MHZ_FALLBACK
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"
+
+
+def rooflines(abytes: float, aflops: float, kernel_ms: float, traffic):
+    """(binding, other) roofline objects of a kernel time: HBM against the measured copy
+    bandwidth, FP32 ALU against the device's FMA peak; the binding one has the longer ideal time."""
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else HBM_PEAK_FALLBACK
+    alu_peak, alu_src = device_alu_peak()
+    hbm_ach = abytes / (kernel_ms * 1e-3) / 1e9
+    alu_ach = aflops / (kernel_ms * 1e-3) / 1e12
+    hbm_obj = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
+               "traffic": traffic, "algorithmic_bytes": abytes, "peak_source": "measured" if peaks else "fallback"}
+    alu_obj = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
+               "traffic": traffic, "algorithmic_flops": aflops, "peak_source": alu_src}
+    t_hbm, t_alu = abytes / (hbm_peak * 1e9), aflops / (alu_peak * 1e12)
+    return (alu_obj, hbm_obj) if t_alu > t_hbm else (hbm_obj, alu_obj)
 
 
 def algorithmic_bytes(E, N, nnz, nen, q, s=4):
@@ -150,16 +193,20 @@ def make(workload: str, n=None):
 def cpu_oracle_sample(w, budget_s: float):
     """Oracle throughput on the first elements of the workload (all equations), single thread."""
     import oracle as O
-    m, f = w.mesh, w.fields.astype(np.float32).astype(np.float64)
-    rp, ci, _ = O.pattern(m.elem_type, m.conn, m.n_node, with_pos=False)
-    q = f.n_eq
-    t0 = time.perf_counter()
+    m = w.mesh
+    q = w.fields.n_eq
     n0 = 64 if m.elem_type == G.HEX27 else 512
-    O.assemble(m.elem_type, m.coords, m.conn, rp, ci, f, e_range=(0, n0))
+    c0, k0, a0 = _oracle_submesh(m, w.fields, 0, n0)
+    rp0, ci0, _ = O.pattern(m.elem_type, k0, c0.shape[0], with_pos=False)
+    t0 = time.perf_counter()
+    O.assemble(m.elem_type, c0, k0, rp0, ci0, G.Fields(*a0, w.fields.dt))
     rate = n0 / max(time.perf_counter() - t0, 1e-9)
     ne = int(min(m.n_elem, max(n0, rate * budget_s)))
+    c, k, a = _oracle_submesh(m, w.fields, 0, ne)
+    rp, ci, _ = O.pattern(m.elem_type, k, c.shape[0], with_pos=False)
+    f = G.Fields(*a, w.fields.dt)
     t0 = time.perf_counter()
-    O.assemble(m.elem_type, m.coords, m.conn, rp, ci, f, e_range=(0, ne))
+    O.assemble(m.elem_type, c, k, rp, ci, f)
     dt = time.perf_counter() - t0
     return ne, q, dt, (rp, ci)
 
@@ -168,7 +215,8 @@ def _oracle_submesh(m, f, e0, e1):
     """Elements [e0, e1) as a compact mesh: their nodes renumbered in ascending order."""
     conn = m.conn[e0:e1]
     nodes, inv = np.unique(conn, return_inverse=True)
-    arrays = tuple(np.ascontiguousarray(a[:, nodes]) for a in (f.velocity, f.diffusivity, f.reaction, f.phi_old))
+    arrays = tuple(np.ascontiguousarray(a[:, nodes].astype(np.float32).astype(np.float64))
+                   for a in (f.velocity, f.diffusivity, f.reaction, f.phi_old))
     return np.ascontiguousarray(m.coords[nodes]), inv.reshape(conn.shape).astype(np.int32), arrays
 
 
@@ -199,7 +247,7 @@ def oracle_all_cores(w, per_worker_s: float, reps: int):
     import multiprocessing as mp
     import oracle as O
     m = w.mesh
-    f = w.fields.astype(np.float32).astype(np.float64)
+    f = w.fields  # each chunk's columns are rounded to FP32 (the arrays the GPU path consumes)
     q = f.n_eq
     procs = max(1, len(os.sched_getaffinity(0)))
     n0 = 64 if m.elem_type == G.HEX27 else 512
@@ -245,7 +293,8 @@ def run_reference(args, w, rank):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config_dict(args.workload, w, None),
+           "config": dict(config_dict(args.workload, w, closed_form_nnz(args.workload, m.n_cells)),
+                          sampled=f"each step times elements [0, {ne}) of {m.n_elem}"),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -308,9 +357,22 @@ def main():
     ap.add_argument("--graph", type=int, default=None,
                     help="1: time the K steps as one CUDA graph of K (assemble, field update) time steps "
                          "(default on for hex8_256_32eq)")
+    ap.add_argument("--side", default=None,
+                    help="comma-separated further workloads measured after the headline one (their results go "
+                         "into 'workloads'); default: the other paper-shaped workloads when the headline is the "
+                         "default workload on one GPU, 'none' to skip")
     args = ap.parse_args()
     if args.graph is None:
         args.graph = 1 if args.workload == "hex8_256_32eq" else 0
+    if args.side is None:
+        args.side = list(SIDE_WORKLOADS) if (args.workload == DEFAULT_WORKLOAD and args.cells is None) else []
+    elif args.side == "none":
+        args.side = []
+    else:
+        args.side = [x for x in args.side.split(",") if x]
+        bad = [x for x in args.side if x not in WORKLOADS]
+        if bad:
+            ap.error(f"unknown side workloads: {bad}")
     rank, world, local = dist_env()
     if args.workload in MIXED_WORKLOADS:
         run_mixed(args, rank, world, local)
@@ -319,6 +381,7 @@ def main():
     if args.impl == "reference":
         run_reference(args, w, rank)
         return
+    w0 = w  # the workload as drawn (the graph mode replaces w with the stepped field for its parity check)
 
     import torch
     from paper_2107_11541_gb300 import fea
@@ -409,17 +472,7 @@ def main():
     nen = NEN[m.elem_type]
     abytes = algorithmic_bytes(m.n_elem, m.n_node, nnz, nen, q)
     aflops = algorithmic_flops_per_elem_eq(nen) * m.n_elem * q
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    hbm_ach = abytes / (kernel_ms * 1e-3) / 1e9
-    alu_ach = aflops / (kernel_ms * 1e-3) / 1e12
-    t_hbm, t_alu = abytes / (hbm_peak * 1e9), aflops / (alu_peak * 1e12)
-    hbm_obj = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
-               "traffic": profiled_traffic(args.workload), "algorithmic_bytes": abytes,
-               "peak_source": "measured" if peaks else "fallback"}
-    alu_obj = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
-               "traffic": hbm_obj["traffic"], "algorithmic_flops": aflops,
-               "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
-    roof, other = (alu_obj, hbm_obj) if t_alu > t_hbm else (hbm_obj, alu_obj)
+    roof, other = rooflines(abytes, aflops, kernel_ms, profiled_traffic(args.workload))
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -555,9 +608,11 @@ def main():
         values = torch.empty((q, nnz), dtype=torch.float32, device="cuda")
 
     if not args.no_e2e:
-        out["e2e"] = end_to_end(h, p, f32, m, nnz, q, stream, min(args.steps, 5), world, dist)
+        out["e2e"] = end_to_end(h, p, f32, m, nnz, q, stream, min(args.steps, 5), world, dist, values_dev=values,
+                                parity_of=(w0, None) if rank == 0 and not args.no_parity else None)
 
     if rank == 0 and world == 1 and not args.no_cpu:
+        w = w0
         ne, qq, dt, _ = cpu_oracle_sample(w, args.cpu_budget)
         single = {"value": ne * qq / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                   "sample": f"elements [0, {ne}) of {m.n_elem}, all {qq} equations, FP64 C oracle, single thread"}
@@ -568,10 +623,95 @@ def main():
         out["cpu_baseline_single"] = single
     fea.fea_pattern_destroy(p)
     fea.fea_mesh_destroy(h)
+    if world == 1 and args.side:
+        del values, rhs, dev
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        out["workloads"] = {nm: side_workload(nm, max(3, min(args.steps, 10)), args.warmup, not args.no_parity)
+                            for nm in args.side}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def side_workload(name: str, steps: int, warmup: int, parity: bool):
+    """One more paper-shaped workload measured like the headline one (device-resident inputs, the
+    autotuned FP32 fused path, CUDA events around every assembly), with its rooflines, clocks,
+    sampled parity against the oracle and the plain FP64 path on the same GPU."""
+    import torch
+    from paper_2107_11541_gb300 import fea
+    w = make(name)
+    m, fld = w.mesh, w.fields
+    q = fld.n_eq
+    stream = torch.cuda.Stream()
+    h = fea.fea_mesh_create(m.coords, m.conn, m.elem_type, stream)
+    p = fea.fea_pattern_build(h)
+    nnz = fea.fea_pattern_get(p)[3]
+    f32 = fld.astype(np.float32)
+    with torch.cuda.stream(stream):
+        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (f32.velocity, f32.diffusivity,
+                                                                          f32.reaction, f32.phi_old)]
+        values = torch.empty((q, nnz), dtype=torch.float32, device="cuda")
+        rhs = torch.empty((q, m.n_node), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    opts = fea.fea_default_opts()
+    for _ in range(warmup):
+        fea.fea_assemble(h, p, *dev, fld.dt, q, opts, values, rhs)
+    fea.fea_sync(h)
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in kev:
+        a.record(stream)
+        b.record(stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    for a, b in kev:
+        opts.event_begin, opts.event_end = a.cuda_event, b.cuda_event
+        fea.fea_assemble(h, p, *dev, fld.dt, q, opts, values, rhs)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    opts.event_begin = opts.event_end = None
+    fea.fea_sync(h)
+    kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
+    nen = NEN[m.elem_type]
+    roof, other = rooflines(algorithmic_bytes(m.n_elem, m.n_node, nnz, nen, q),
+                            algorithmic_flops_per_elem_eq(nen) * m.n_elem * q, kernel_ms, profiled_traffic(name))
+    res = {"config": config_dict(name, w, nnz), "steps": steps, "warmup": warmup, "kernel_ms": kernel_ms,
+           "value": m.n_elem * q / (kernel_ms * 1e-3), "unit": UNIT, "roofline": roof, "roofline_other": other,
+           "clocks": clk}
+    try:
+        sc, gr = fea.fea_tuned_strategy(p, q)
+        res["config"]["scatter"] = {1: "atomic", 2: "rowowned", 3: "gather"}.get(sc, str(sc))
+        res["config"]["eq_groups"] = gr
+    except fea.FeaError:
+        pass
+    if parity:
+        res["parity"] = sampled_parity(w, values, rhs, p, nnz)
+    del values
+    q64 = q if m.n_elem * q <= 60_000_000 else 4
+    d64 = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+           for a in (fld.velocity, fld.diffusivity[:q64], fld.reaction[:q64], fld.phi_old[:q64])]
+    v64 = torch.empty((q64, nnz), dtype=torch.float64, device="cuda")
+    r64 = torch.empty((q64, m.n_node), dtype=torch.float64, device="cuda")
+    o64 = fea.fea_default_opts(precision=fea.FEA_F64_PLAIN)
+    fea.fea_assemble(h, p, *d64, fld.dt, q64, o64, v64, r64)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fea.fea_assemble(h, p, *d64, fld.dt, q64, o64, v64, r64)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t64 = a.elapsed_time(b)
+    v_f64 = m.n_elem * q64 / (t64 * 1e-3)
+    res["fp64_plain"] = {"value": v_f64, "unit": UNIT, "ms_per_step": t64, "equations_timed": q64,
+                         "speedup_f32_fused": res["value"] / v_f64}
+    del v64, r64, d64, dev, rhs
+    fea.fea_pattern_destroy(p)
+    fea.fea_mesh_destroy(h)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return res
 
 
 def make_mixed(workload: str, n=None):
@@ -666,20 +806,10 @@ def run_mixed(args, rank, world, local):
     ms = t0e.elapsed_time(t1e) / args.steps
     kernel_ms = sum(a.elapsed_time(b) for a, b in kev) / len(kev)
     ms, kernel_ms, value = aggregate_over_ranks(ms, kernel_ms, mm.n_elem * q, world, dist, "cuda")
-    peaks = measured_peaks()
-    hbm_peak = peaks["hbm_gbs"] if peaks else HBM_PEAK_FALLBACK
     abytes = sum(4 * c.size for _, c in mm.blocks) + 6 * mm.n_node * 4 + 3 * q * mm.n_node * 4 + \
         q * (nnz + mm.n_node) * 4
     aflops = sum(algorithmic_flops_per_elem_eq(G.NEN[t], NG[t]) * c.shape[0] for t, c in mm.blocks) * q
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    hbm_ach, alu_ach = abytes / (kernel_ms * 1e-3) / 1e9, aflops / (kernel_ms * 1e-3) / 1e12
-    hbm_obj = {"bound": "hbm", "achieved": hbm_ach, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_ach / hbm_peak,
-               "traffic": None, "algorithmic_bytes": abytes, "peak_source": "measured" if peaks else "fallback"}
-    alu_obj = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_ach / alu_peak,
-               "traffic": None, "algorithmic_flops": aflops,
-               "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
-    t_hbm, t_alu = abytes / (hbm_peak * 1e9), aflops / (alu_peak * 1e12)
-    roof, other = (alu_obj, hbm_obj) if t_alu > t_hbm else (hbm_obj, alu_obj)
+    roof, other = rooflines(abytes, aflops, kernel_ms, None)
     config = {"workload": args.workload, "elem_types": {G.NAMES[t]: int(c.shape[0]) for t, c in mm.blocks},
               "elements": mm.n_elem, "nodes": mm.n_node, "nnz": int(nnz), "n_eq": q, "precision": "f32_fused",
               "l2": "no flush: inputs + outputs per step exceed the 129 MB L2", "scatter": "atomic"}
@@ -730,18 +860,22 @@ def run_mixed(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def sampled_parity(w, values, rhs, p, nnz, n_rows=48, seed=5, terms=None):
-    """Sampled full-size rows against the oracle (computed row by row from incident elements)."""
+def sampled_parity(w, values, rhs, p, nnz, n_rows=48, seed=5, terms=None, wide=None):
+    """Sampled full-size rows against the oracle (computed row by row from incident elements).
+    values/rhs may be device or host tensors; ``wide`` is the FP32 fields widened to FP64 (made
+    here when not given)."""
     import oracle as O
     from paper_2107_11541_gb300 import fea
     m = w.mesh
     rp_t, ci_t, _ = fea.pattern_tensors(p, m.n_node, 0, NEN[m.elem_type])
     rp = rp_t.cpu().numpy()
-    rs = O.RowSampler(m.elem_type, m.coords, m.conn, w.fields.astype(np.float32).astype(np.float64),
-                      O.ALL_TERMS if terms is None else terms)
+    if wide is None:
+        wide = w.fields.astype(np.float32).astype(np.float64)
+    rs = O.RowSampler(m.elem_type, m.coords, m.conn, wide, O.ALL_TERMS if terms is None else terms)
     rng = np.random.default_rng(seed)
     rows = np.unique(np.concatenate([[0, m.n_node - 1], rng.integers(0, m.n_node, n_rows)]))
     worst_a = worst_b = 0.0
+    plain = (0.0, 0.0)
     for r in rows:
         cols, ref, _, refb, absb = rs.row(r)
         k0, k1 = rp[r], rp[r + 1]
@@ -750,15 +884,53 @@ def sampled_parity(w, values, rhs, p, nnz, n_rows=48, seed=5, terms=None):
         ea = np.sqrt(((got - ref) ** 2).sum(axis=1) / (ref ** 2).sum(axis=1)).max()
         gb = rhs[:, r].double().cpu().numpy()
         eb = (np.abs(gb - refb) / np.where(absb > 0, absb, 1.0)).max()
+        nz = np.abs(refb) > 0
+        if nz.any():
+            pl = np.abs(gb - refb)[nz] / np.abs(refb)[nz]
+            i = int(np.argmax(pl))
+            if pl[i] > plain[0]:
+                plain = (float(pl[i]), float(absb[nz][i] / np.abs(refb)[nz][i]))
         worst_a, worst_b = max(worst_a, ea), max(worst_b, eb)
     return {"rows": int(len(rows)), "max_row_err_A": worst_a, "max_err_b": worst_b, "tol": 1e-5,
-            "pass": bool(worst_a <= 1e-5 and worst_b <= 1e-5)}
+            "pass": bool(worst_a <= 1e-5 and worst_b <= 1e-5),
+            "max_err_b_plain": plain[0], "cancellation_ratio_of_that_row": plain[1],
+            "err_b_definitions": "max_err_b = |b - b*| / (sum of the magnitudes of b*'s Gauss-point summands); "
+                                 "max_err_b_plain = |b - b*| / |b*|"}
 
 
-def end_to_end(h, p, f32, m, nnz, q, stream, steps, world, dist):
-    """Same metric through fea_assemble_host: pinned host inputs copied in, values and RHS read back."""
+def host_memory_available() -> int:
+    """Bytes this process can still take on the host: MemAvailable, capped by the cgroup limit."""
+    avail = None
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    try:
+        lim = open("/sys/fs/cgroup/memory.max").read().strip()
+        cur = int(open("/sys/fs/cgroup/memory.current").read().strip())
+        if lim != "max":
+            left = int(lim) - cur
+            avail = left if avail is None else min(avail, left)
+    except (OSError, ValueError):
+        pass
+    return avail if avail is not None else 0
+
+
+def end_to_end(h, p, f32, m, nnz, q, stream, steps, world, dist, values_dev=None, parity_of=None):
+    """Same metric through fea_assemble_host: pinned host inputs copied in, values and RHS read back.
+    Also the copy floor of this box: one cudaMemcpyAsync per direction of the step's bytes between
+    pinned host memory and the device (values_dev, the device-resident values of the same size, is
+    the device end of the output copy), and, when ``parity_of`` = (workload, wide fields) is given,
+    sampled rows of the last step's host outputs against the oracle."""
     import torch
     from paper_2107_11541_gb300 import fea
+    need = 4 * (f32.velocity.size + f32.diffusivity.size + f32.reaction.size + f32.phi_old.size + q * (nnz + m.n_node))
+    avail = host_memory_available()
+    if need > 0.6 * avail:  # pinned host buffers this large would crowd the host
+        return {"skipped": f"the pinned host buffers ({need / 1e9:.1f} GB) exceed 60% of the host memory "
+                           f"available to this process ({avail / 1e9:.1f} GB)"}
     pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
            for a in (f32.velocity, f32.diffusivity, f32.reaction, f32.phi_old)]
     hv = torch.empty((q, nnz), dtype=torch.float32).pin_memory()
@@ -779,8 +951,36 @@ def end_to_end(h, p, f32, m, nnz, q, stream, steps, world, dist):
         t = float(tt[0])
     h2d = sum(x.numel() * 4 for x in pin)
     d2h = (hv.numel() + hr.numel()) * 4
-    return {"value": m.n_elem * q * world / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": t * 1e3}
+    out = {"value": m.n_elem * q * world / t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": t * 1e3, "api": "fea_assemble_host"}
+    if values_dev is not None:
+        # the copy floor: the largest input and the values, one copy each way, CUDA events on the stream
+        big = max(pin, key=lambda x: x.numel())
+        dbig = torch.empty(big.shape, dtype=big.dtype, device="cuda")
+        ea, eb, ec = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        with torch.cuda.stream(stream):
+            dbig.copy_(big, non_blocking=True)
+            ea.record(stream)
+            dbig.copy_(big, non_blocking=True)
+            eb.record(stream)
+            hv.copy_(values_dev, non_blocking=True)
+            ec.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = big.numel() * 4 / (ea.elapsed_time(eb) * 1e-3) / 1e9
+        d2h_gbs = hv.numel() * 4 / (eb.elapsed_time(ec) * 1e-3) / 1e9
+        floor_ms = (h2d / h2d_gbs + d2h / d2h_gbs) / 1e9 * 1e3
+        out["copy_floor"] = {"h2d_gbs": h2d_gbs, "d2h_gbs": d2h_gbs, "ms": floor_ms,
+                             "what": "one cudaMemcpyAsync per direction between pinned host memory and the "
+                                     "device (largest input array, then the values), CUDA events; ms = the "
+                                     "step's bytes at those rates, copies not overlapped"}
+        del dbig
+        # the timed steps ended with values on the host: redo one so the parity check sees them
+        fea.fea_assemble_host(h, p, *pin, f32.dt, q, opts, hv, hr)
+    if parity_of is not None:
+        wl, wide = parity_of
+        out["parity"] = sampled_parity(wl, hv, hr, p, nnz, wide=wide)
+    del pin, hv, hr
+    return out
 
 
 if __name__ == "__main__":

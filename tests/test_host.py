@@ -199,3 +199,19 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(fea.lib, "__defaults__", (missing,))
     with pytest.raises(FileNotFoundError):
         fea.fea_version()
+
+
+def test_bench_closed_form_nnz():
+    """The reference arm reports nnz from counting formulas; they give the pattern sizes the
+    oracle's own pattern reaches (pinned in the oracle tests), and the oracle's count on small
+    grids of every workload's element type."""
+    import bench
+    import oracle as O
+    want = {"tet4_100_perm_1eq": 15_210_901, "hex8_128_21eq": 57_066_625, "hex27_48_11eq": 57_066_625,
+            "hex8_256_32eq": 454_756_609}
+    for wl, nnz in want.items():
+        assert bench.closed_form_nnz(wl) == nnz
+    for wl in want:
+        m = G.make_mesh(bench.WORKLOADS[wl], n=3)
+        rp, _, _ = O.pattern(m.elem_type, m.conn, m.n_node, with_pos=False)
+        assert bench.closed_form_nnz(wl, 3) == rp[-1]
