@@ -340,6 +340,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(MIXED_WORKLOADS))
     ap.add_argument("--scatter", type=int, default=0, help="0 auto, 1 atomic, 2 row-owned, 3 gather")
+    ap.add_argument("--contraction", type=int, default=0,
+                    help="Hex27 element matrices: 0 auto, 1 CUDA cores, 2 tensor cores bf16x3, 3 tensor cores bf16x6")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
@@ -404,7 +406,7 @@ def main():
         values = torch.empty((q, nnz), dtype=torch.float32, device="cuda")
         rhs = torch.empty((q, m.n_node), dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
-    opts = fea.fea_default_opts(scatter=args.scatter)
+    opts = fea.fea_default_opts(scatter=args.scatter, contraction=args.contraction)
 
     def step(ev=None):
         if ev is not None:

@@ -108,6 +108,16 @@ typedef enum {
                                ascending element order and written once (deterministic) */
 } fea_scatter;
 
+typedef enum {
+  FEA_CONTRACT_AUTO = 0,      /* autotuned with the scatter (see FEA_SCATTER_AUTO); CUDA cores when not tuned */
+  FEA_CONTRACT_CUDA = 1,      /* FP32 products on the CUDA cores */
+  FEA_CONTRACT_TC_BF16X3 = 2, /* tensor cores: each operand split into two BF16 parts, products
+                                 hi hi + hi lo + lo hi (about 16 bits of each operand), FP32 accumulation */
+  FEA_CONTRACT_TC_TF32X3 = 3  /* tensor cores: two TF32 parts (the value with its 13 low mantissa bits
+                                 cleared, and the exact remainder), the same three products (about 22
+                                 bits of each operand), FP32 accumulation */
+} fea_contraction;
+
 typedef struct {
   int32_t precision;        /* fea_precision, default FEA_F32_FUSED */
   int32_t terms;            /* bit mask of FEA_TERM_*, default FEA_TERM_ALL */
@@ -127,7 +137,9 @@ typedef struct {
                                each part's values copied back while the next part computes (at most
                                n_eq); 0 = automatic: 3 when the values exceed 256 MB and n_eq >= 3,
                                else 1.  Default 0 */
-  int32_t reserved[1];
+  int32_t contraction;      /* fea_contraction: how the FP32 Hex27 element matrices (full operator, up to
+                               12 equations) are contracted; other element types and the residual use
+                               the CUDA cores.  Default FEA_CONTRACT_AUTO */
 } fea_assemble_opts;
 
 /* Fills *opts with the defaults listed above. */

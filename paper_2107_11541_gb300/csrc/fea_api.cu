@@ -376,6 +376,8 @@ static fea_status check_assemble_args(fea_mesh* m, const fea_pattern* p, const v
   if (o->cancel_check != 0 && o->cancel_check != 1) return fail(FEA_ERR_ARG, "cancel_check must be 0 or 1");
   if (o->cancel_check && o->accumulate) return fail(FEA_ERR_ARG, "cancel_check cannot be combined with accumulate");
   if (o->host_parts < 0) return fail(FEA_ERR_ARG, "host_parts must be >= 0");
+  if (o->contraction < FEA_CONTRACT_AUTO || o->contraction > FEA_CONTRACT_TC_TF32X3)
+    return fail(FEA_ERR_ARG, "unknown contraction");
   if (m->mixed && (o->scatter == FEA_SCATTER_ROWOWNED || o->scatter == FEA_SCATTER_GATHER || o->cancel_check))
     return fail(FEA_ERR_ARG, "a mesh of several element types scatters with atomics (no row-owned, gather or "
                              "cancellation check)");
@@ -425,6 +427,7 @@ static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, 
   a.kappa_threshold = o->kappa_threshold;
   a.status = m->status;
   a.elem_order = (!m->mixed && m->type == FEA_TET4) ? p->elem_order : nullptr;
+  a.contraction = o->contraction == FEA_CONTRACT_AUTO ? FEA_CONTRACT_CUDA : o->contraction;
   return a;
 }
 

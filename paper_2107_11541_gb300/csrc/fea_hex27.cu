@@ -23,9 +23,28 @@
 //   9. out: A = P^T Q + diffusion (the D entry of (a, b) from a table), to the gather
 //      scratch em[e][entry][q], as atomic adds into the CSR values and RHS (one position
 //      load per entry for all equations), or as the matrix-free residual.
+//
+// Tensor-core variant (TCP = 2: BF16 parts, TCP = 4: TF32 parts): steps 5b-8 become one matrix
+// product per element on the fifth-generation tensor cores.  For equation q the element matrix
+// is A_q = L_q R^T with the right factor shared by all equations and the left factor per
+// equation (K = 135 = 27 + 27 + 81):
+//   R[b][k] = [ N_b(g) | u.grad N_b(g) | grad N_b(g) (3 per g) ],
+//   L_q[a][k] = [ (1/dt + s) P_a(g) | P_a(g) | dV k_g grad N_a(g) ],
+// so that sum_k L_q[a][k] R[b][k] = sum_g P_a Q_b + dV k_g D_ab.  The rows (q, a) of all
+// equations are stacked (m = 27 q + a) into 128-row tiles; each tile is one M = 128, N = 32
+// product over K (zero padded to whole instructions) accumulated in tensor memory, columns
+// 32 t .. 32 t + 31 for tile t.  Each FP32 operand is split in two parts x = x_hi + x_lo and
+// three products hi hi + hi lo + lo hi are summed: with BF16 parts ("bf16x3") about 16 bits
+// of each operand survive, with TF32 parts (x_hi = x with its 13 low mantissa bits cleared,
+// x_lo = x - x_hi, "3xTF32") about 22.  The tiles are built and multiplied in K chunks through
+// two buffers, so that one chunk is built while the tensor cores multiply the previous one.
+// The RHS b_a = sum_g P_a(g) phi_g / dt is formed on the CUDA cores.
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "fea_internal.cuh"
+#include "fea_tc.cuh"
 
 namespace fea {
 namespace {
@@ -43,12 +62,31 @@ constexpr int H27_QMAX = 12;
 static_assert(H27_QMAX * 2 * NB + NBP * (H27_QMAX / 4) <= H27_THREADS, "one task per thread");
 static_assert(NBP * BPS <= DQS && DQS % 4 == 0 && H27_QMAX * DQS <= NN * DSTRIDE, "diffusion sums fit where D was");
 
+// Tensor-core operand shapes for element size ES (2: BF16, 4: TF32).  A core-matrix row is 16
+// bytes (VPC values); an instruction covers K = 2 core columns (32 bytes); K = 135 is padded to
+// whole instructions; a chunk is CS instructions of one 128-row tile.
+template <int ES>
+struct TcShape {
+  static constexpr int VPC = 16 / ES;
+  static constexpr int KP = ES == 2 ? 144 : 136;
+  static constexpr int KC = KP / VPC;                 // core columns: 18 or 34
+  static constexpr int STEPS = KC / 2;                // instructions per tile: 9 or 17
+  static constexpr int CS = ES == 2 ? 3 : 6;          // instructions per chunk
+  static constexpr int NCH = (STEPS + CS - 1) / CS;   // chunks per tile: 3
+  static constexpr int PLANE_B = 32 * KC * 16;        // bytes of one part of R (32 rows)
+  static constexpr int PLANE_C = 128 * 2 * CS * 16;   // bytes of one part of a chunk (128 rows)
+};
+constexpr int TC_M = 128, TC_N = 32;                  // one MMA tile
+constexpr int TC_TMEM_COLS = 128;                     // 3 tiles x 32 columns, rounded to a power of two
+static_assert(TcShape<2>::NCH == 3 && TcShape<4>::NCH == 3, "three chunks per tile");
+
 // Shared-memory layout in floats; QP = equations padded to a multiple of 4; SR staged rows
 // of 27 node values (padded to 28): x hi (3), x lo (3), u (3), then k, s, phi_old per equation.
 struct H27Layout {
   int QP, SR, nt, dnt, rowp, wq, sym, bpt, cn, stage, spos, xd, jg, dv, un, ug, gr, ua, kgt, pg, tau, sig, p, q, d,
       misc, total;
-  __host__ __device__ H27Layout(int Q) {
+  int tiles, cf, opb, opa, mbar, tslot;  // tensor-core variant only
+  __host__ __device__ H27Layout(int Q, int tcp = 0) {
     QP = (Q + 3) & ~3;
     SR = 9 + 3 * Q;
     int o = 0;
@@ -76,13 +114,30 @@ struct H27Layout {
     tau = o;   o += Q * NN;
     sig = o;   o += Q * NN;            // 1/dt + s_g
     o = (o + 3) & ~3;
-    p = o;     o += Q * NN * PAD;      // P [q][g][a]; after the contractions P^T Q [q][a][b], b = 27: RHS
-    q = o;     o += Q * NN * PAD;      // Q [q][g][b]
-    d = o;     o += NN * DSTRIDE;      // D [g][pair][BPS]; after the contractions the diffusion sums [q][pair][BPS]
-    misc = o;  o += 4;                 // h
+    tiles = cf = opb = opa = mbar = tslot = 0;
+    if (tcp == 0) {
+      p = o;     o += Q * NN * PAD;      // P [q][g][a]; after the contractions P^T Q [q][a][b], b = 27: RHS
+      q = o;     o += Q * NN * PAD;      // Q [q][g][b]
+      d = o;     o += NN * DSTRIDE;      // D [g][pair][BPS]; after the contractions the diffusion sums [q][pair][BPS]
+      misc = o;  o += 4;                 // h
+      total = o;
+      return;
+    }
+    tiles = (Q * NN + TC_M - 1) / TC_M;
+    cf = o;    o += 4 * Q * NN;        // per (q, g): dV sigma, dV sigma tau, dV, dV tau (16-byte aligned)
+    misc = o;  o += 4;
+    mbar = o;  o += 4;                 // two 8-byte mbarriers (offset even: 8-byte aligned)
+    tslot = o; o += 4;                 // tensor-memory base address
+    o = (o + 31) & ~31;                // 128-byte aligned operands
+    const int plane_b = tcp == 2 ? TcShape<2>::PLANE_B : TcShape<4>::PLANE_B;
+    const int plane_c = tcp == 2 ? TcShape<2>::PLANE_C : TcShape<4>::PLANE_C;
+    opb = o;   o += 2 * plane_b / 4;   // R, two parts
+    opa = o;   o += 2 * 2 * plane_c / 4;  // two chunk buffers of two parts; the results [q][a][PAD] reuse them
+    p = q = d = opa;
     total = o;
   }
 };
+static_assert(H27_QMAX * NN * PAD * 4 <= 2 * 2 * TcShape<2>::PLANE_C, "the results fit in the chunk buffers");
 
 // Block pair (A <= B) of the 7 x 7 block grid, row-major upper triangle.
 __host__ __device__ inline int block_pair(int A, int B) { return A * NB - A * (A - 1) / 2 + (B - A); }
@@ -98,11 +153,65 @@ __host__ __device__ inline int d_slot(int a, int b) {
   return block_pair(a / 4, b / 4) * BPS + (a & 3) * 4 + (b & 3);
 }
 
-template <bool EM>
+// Entry k of the shared right factor for node b: [N_b(g) | u.grad N_b(g) | grad N_b(g)], zero
+// in the padding (b >= 27 or k >= 135).
+__device__ __forceinline__ float tc_rval(const float* sm, const H27Layout& L, int b, int k) {
+  if (b >= NN) return 0.f;
+  if (k < NN) return sm[L.nt + k * PAD + b];
+  if (k < 2 * NN) return sm[L.ua + (k - NN) * PAD + b];
+  if (k < 5 * NN) {
+    const int j = k - 2 * NN, g = j / 3, i = j - 3 * g;
+    return sm[L.gr + (g * 3 + i) * PAD + b];
+  }
+  return 0.f;
+}
+
+// Entry k of equation q's left factor for node a: [(1/dt + s) P_a(g) | P_a(g) | dV k_g grad N_a(g)],
+// P_a = dV (N_a + tau u.grad N_a), from the coefficients cf[q][g] = (dV sigma, dV sigma tau, dV, dV tau).
+__device__ __forceinline__ float tc_lval(const float* sm, const H27Layout& L, int q, int a, int k) {
+  if (k < 2 * NN) {
+    const int g = k < NN ? k : k - NN;
+    const float4 c = reinterpret_cast<const float4*>(sm + L.cf)[q * NN + g];
+    const float n = sm[L.nt + g * PAD + a], u = sm[L.ua + g * PAD + a];
+    return k < NN ? fmaf(c.y, u, c.x * n) : fmaf(c.w, u, c.z * n);
+  }
+  if (k < 5 * NN) {
+    const int j = k - 2 * NN, g = j / 3, i = j - 3 * g;
+    return sm[L.kgt + g * L.QP + q] * sm[L.gr + (g * 3 + i) * PAD + a];
+  }
+  return 0.f;
+}
+
+// One 16-byte core-matrix row of VPC consecutive values in two parts x = hi + lo: BF16 (hi the
+// rounded value, lo the rounded remainder) or TF32 (hi with the 13 low mantissa bits cleared,
+// lo = x - hi, exact).
+template <int ES>
+__device__ __forceinline__ void split_row(const float* v, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+  if constexpr (ES == 2) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      const __nv_bfloat162 r = __floats2bfloat162_rn(v[2 * j] - __low2float(b), v[2 * j + 1] - __high2float(b));
+      h[j] = *reinterpret_cast<const uint32_t*>(&b);
+      l[j] = *reinterpret_cast<const uint32_t*>(&r);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      h[j] = __float_as_uint(v[j]) & 0xFFFFE000u;
+      l[j] = __float_as_uint(v[j] - __uint_as_float(h[j]));
+    }
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <bool EM, int TCP>
 __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
-  extern __shared__ __align__(16) float sm27[];
+  extern __shared__ __align__(128) float sm27[];
   const int Q = p.eq_count;
-  const H27Layout L(Q);
+  const H27Layout L(Q, TCP);
   const int tid = threadIdx.x;
   const int64_t N = p.n_node;
   const float inv_dt = (float)(1.0 / p.dt);
@@ -147,7 +256,21 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
   // the first element's connectivity (plain loads) and node data (cp.async)
   if (blockIdx.x < p.n_elem && tid < NN)
     reinterpret_cast<int*>(sm27 + L.cn)[tid] = p.conn[(int64_t)blockIdx.x * NN + tid];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sm27 + L.mbar);
+  uint32_t tmem = 0, phase0 = 0, phase1 = 0;
+  if constexpr (TCP > 0) {
+    if (tid == 0) {
+      tc::mbar_init(mbar, 1);
+      tc::mbar_init(mbar + 1, 1);
+    }
+    if (tid < 32) tc::tmem_alloc(reinterpret_cast<uint32_t*>(sm27 + L.tslot), TC_TMEM_COLS);
+    tc::fence_before_sync();
+  }
   __syncthreads();
+  if constexpr (TCP > 0) {
+    tc::fence_after_sync();
+    tmem = *reinterpret_cast<const uint32_t*>(sm27 + L.tslot);
+  }
   // staged node data of element e into buffer buf (connectivity already in cn[buf])
   auto stage_issue = [&](int64_t e, int buf) {
     const int* cb = reinterpret_cast<const int*>(sm27 + L.cn + buf * PAD);
@@ -286,10 +409,12 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
           pg = fmaf(n.w, ph.w, pg);
         }
         const float den = c_k * kg + c_u * sm27[L.un + g] + sg;
-        sm27[L.kgt + g * L.QP + q] = sm27[L.dv + g] * kg;
+        const float dvg = sm27[L.dv + g], tg = den > 0.f ? 1.0f / den : 0.f, sgm = inv_dt + sg;
+        sm27[L.kgt + g * L.QP + q] = dvg * kg;
         sm27[L.pg + i] = pg;
-        sm27[L.tau + i] = den > 0.f ? 1.0f / den : 0.f;
-        sm27[L.sig + i] = inv_dt + sg;
+        sm27[L.tau + i] = tg;
+        sm27[L.sig + i] = sgm;
+        if (TCP) reinterpret_cast<float4*>(sm27 + L.cf)[i] = make_float4(dvg * sgm, dvg * sgm * tg, dvg, dvg * tg);
       }
       for (int i = tid; i < NN * (L.QP - Q); i += H27_THREADS) {  // padded equations of k_g: zero
         const int g = i / (L.QP - Q), q = Q + (i - g * (L.QP - Q));
@@ -297,7 +422,7 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
       }
     }
     // 5b. D_ab(g) = grad N_a . grad N_b in 4 x 4 blocks (A <= B), one thread per (g, block pair)
-    for (int i = tid; i < NN * NBP; i += H27_THREADS) {
+    for (int i = tid; i < (TCP ? 0 : NN * NBP); i += H27_THREADS) {
       const int g = i / NBP, bp = i - g * NBP, AB = bpt[bp], A = AB & 0xff, B = AB >> 8;
       const float* gg = sm27 + L.gr + g * 3 * PAD;
       float4 xa[3], xb[3];
@@ -319,6 +444,119 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
       }
     }
     __syncthreads();
+    if constexpr (TCP > 0) {
+      using S = TcShape<TCP>;
+      constexpr int VPC = S::VPC;
+      // TC 1. the shared right factor R, one 16-byte core row (node b, VPC consecutive k) per item
+      unsigned char* opb = reinterpret_cast<unsigned char*>(sm27 + L.opb);
+      for (int it = tid; it < TC_N * S::KC; it += H27_THREADS) {
+        const int b = it & (TC_N - 1), kc = it / TC_N;
+        float v[VPC];
+#pragma unroll
+        for (int j = 0; j < VPC; ++j) v[j] = tc_rval(sm27, L, b, kc * VPC + j);
+        uint4 hi, lo;
+        split_row<TCP>(v, hi, lo);
+        unsigned char* dst = opb + ((b >> 3) * S::KC + kc) * 128 + (b & 7) * 16;
+        *reinterpret_cast<uint4*>(dst) = hi;
+        *reinterpret_cast<uint4*>(dst + S::PLANE_B) = lo;
+      }
+      cp_async_wait_all();  // the next element's connectivity
+      __syncthreads();
+      if (en < p.n_elem) stage_issue(en, cur ^ 1);  // the next element's node data starts to arrive
+      // TC 2. chunks (tile t, instructions s0 .. s0 + CS - 1): built into buffer c & 1 while the
+      // tensor cores multiply the chunk before; one thread issues each chunk's products
+      constexpr int PA[3] = {0, 0, 1}, PB[3] = {0, 1, 0};  // parts: hi hi, hi lo, lo hi
+      bool ok = true;
+      int pend0 = 0, pend1 = 0;
+      auto wait_buf = [&](int b) {
+        uint32_t& ph = b ? phase1 : phase0;
+        ok = tc::mbar_wait(mbar + b, ph, 1 << 22) && ok;
+        ph ^= 1u;
+      };
+      unsigned char* opa = reinterpret_cast<unsigned char*>(sm27 + L.opa);
+      for (int c = 0; c < L.tiles * S::NCH; ++c) {
+        const int t = c / S::NCH, j = c - t * S::NCH, bsel = c & 1;
+        const int s0 = j * S::CS, ns = min(S::CS, S::STEPS - s0);
+        if (bsel ? pend1 : pend0) {  // the products that read this buffer must have finished
+          wait_buf(bsel);
+          (bsel ? pend1 : pend0) = 0;
+        }
+        unsigned char* buf = opa + bsel * 2 * S::PLANE_C;
+        for (int it = tid; it < TC_M * 2 * ns; it += H27_THREADS) {
+          const int r = it & (TC_M - 1), lc = it / TC_M, m = t * TC_M + r, q = m / NN, a = m - q * NN;
+          const int k0 = (2 * s0 + lc) * VPC;
+          float v[VPC];
+#pragma unroll
+          for (int jj = 0; jj < VPC; ++jj) v[jj] = q < Q ? tc_lval(sm27, L, q, a, k0 + jj) : 0.f;
+          uint4 hi, lo;
+          split_row<TCP>(v, hi, lo);
+          unsigned char* dst = buf + ((r >> 3) * 2 * S::CS + lc) * 128 + (r & 7) * 16;
+          *reinterpret_cast<uint4*>(dst) = hi;
+          *reinterpret_cast<uint4*>(dst + S::PLANE_C) = lo;
+        }
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          const uint32_t a0 = tc::smem_addr(buf), b0 = tc::smem_addr(opb);
+          for (int ls = 0; ls < ns; ++ls)
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+              const uint64_t da = tc::smem_desc(a0 + PA[pr] * S::PLANE_C + ls * 256, 128, 2 * S::CS * 128);
+              const uint64_t db = tc::smem_desc(b0 + PB[pr] * S::PLANE_B + (s0 + ls) * 256, 128, S::KC * 128);
+              const uint32_t acc = (j > 0 || ls > 0 || pr > 0) ? 1u : 0u;
+              if constexpr (TCP == 2) tc::mma_bf16(tmem + TC_N * t, da, db, tc::idesc_bf16_f32(TC_M, TC_N), acc);
+              else tc::mma_tf32(tmem + TC_N * t, da, db, tc::idesc_tf32_f32(TC_M, TC_N), acc);
+            }
+          tc::commit(mbar + bsel);
+        }
+        (bsel ? pend1 : pend0) = 1;
+      }
+      if (pend0) wait_buf(0);
+      if (pend1) wait_buf(1);
+      tc::fence_after_sync();
+      if (__syncthreads_or(!ok)) {  // a product never completed: report it and stop
+        if (tid == 0) atomicOr(p.status, ST_TIMEOUT);
+        break;
+      }
+      // TC 3. the accumulators to shared memory as [q][a][PAD] (m = 27 q + a): warp w reads the
+      // lanes 32 (w % 4) .. + 31 of every tile, columns 16 (w / 4) .. + 15
+      float* R = sm27 + L.opa;
+      {
+        const int w = tid >> 5, lq = w & 3, ch = w >> 2;
+        for (int t = 0; t < L.tiles; ++t) {
+          float v[16];
+          tc::tmem_ld16(tmem + ((uint32_t)(32 * lq) << 16) + (uint32_t)(TC_N * t + 16 * ch), v);
+          const int m = t * TC_M + 32 * lq + (tid & 31);
+          if (m < Q * NN) {
+            float* dst = R + m * PAD + 16 * ch;
+            reinterpret_cast<float4*>(dst)[0] = make_float4(v[0], v[1], v[2], v[3]);
+            reinterpret_cast<float4*>(dst)[1] = make_float4(v[4], v[5], v[6], v[7]);
+            if (ch == 0) {
+              reinterpret_cast<float4*>(dst)[2] = make_float4(v[8], v[9], v[10], v[11]);
+              reinterpret_cast<float4*>(dst)[3] = make_float4(v[12], v[13], v[14], v[15]);
+            } else {  // columns 24 .. 26; 27 .. 31 are padding (column 27 takes the RHS)
+              dst[8] = v[8];
+              dst[9] = v[9];
+              dst[10] = v[10];
+            }
+          }
+        }
+      }
+      tc::fence_before_sync();
+      // TC 4. the RHS b_a = sum_g P_a(g) phi_g / dt per (q, a), into column 27
+      for (int i = tid; i < Q * NN; i += H27_THREADS) {
+        const int q = i / NN, a = i - q * NN;
+        float sum = 0.f;
+        for (int g = 0; g < NN; ++g) {
+          const int qg = q * NN + g;
+          const float P = sm27[L.dv + g] * fmaf(sm27[L.tau + qg], sm27[L.ua + g * PAD + a], sm27[L.nt + g * PAD + a]);
+          sum = fmaf(P, sm27[L.pg + qg] * inv_dt, sum);
+        }
+        R[i * PAD + NN] = sum;
+      }
+      __syncthreads();
+    } else {
     // 6. P and Q per (q, g, four columns a); the padded column: P 0, Q phi_g / dt (the RHS)
     for (int i = tid; i < Q * NN * NB; i += H27_THREADS) {
       const int qg = i / NB, c4 = (i - qg * NB) * 4, g = qg - (qg / NN) * NN;
@@ -401,6 +639,9 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
       }
     }
     __syncthreads();
+    }  // CUDA-core contraction
+    float* R = sm27 + L.p;   // [q][a][PAD]: the element matrices (CUDA cores: P^T Q only), column 27 the RHS
+    const float* Dq = sm27 + L.d;  // CUDA cores: the diffusion sums [q][DQS]
     // 9. out
     if (p.resid) {  // matrix-free: b_a - sum_b A_ab phi_b, one thread per (q, a)
       for (int i = tid; i < Q * NN; i += H27_THREADS) {
@@ -410,7 +651,7 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
         const uint16_t* sa = symt + a * NN;
         float y = Ra[NN];
         const float* Dr = Dq + q * DQS;
-        for (int b = 0; b < NN; ++b) y = fmaf(-(Ra[b] + Dr[sa[b]]), fq[ce[b]], y);
+        for (int b = 0; b < NN; ++b) y = fmaf(-(Ra[b] + (TCP == 0 ? Dr[sa[b]] : 0.f)), fq[ce[b]], y);
         atomicAdd(p.resid + (int64_t)(p.eq0 + q) * N + ce[a], y);
       }
     } else if (EM) {  // em[e][entry][q]: entry a * 27 + b of A, then 729 + a of the RHS
@@ -421,7 +662,8 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
         float v;
         if (ent < NN * NN) {
           const int a = ent / NN, b = ent - a * NN;
-          v = R[q * RQ + a * PAD + b] + Dq[q * DQS + symt[ent]];
+          v = R[q * RQ + a * PAD + b];
+          if (TCP == 0) v += Dq[q * DQS + symt[ent]];
         } else {
           v = R[q * RQ + (ent - NN * NN) * PAD + NN];
         }
@@ -438,20 +680,29 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
         const int64_t stride = mat ? p.nnz : N;
         for (int q = 0; q < Q; ++q) {
           float v = R[q * RQ + j];
-          if (mat) v += Dq[q * DQS + k];
+          if (TCP == 0 && mat) v += Dq[q * DQS + k];
           atomicAdd(dst + q * stride, v);
         }
       }
     }
   }
   cp_async_wait_all();  // no copy is left in flight when the CTA exits
+  if constexpr (TCP > 0) {  // every tensor-memory load has completed (each thread waited on its own)
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid < 32) tc::tmem_dealloc(tmem, TC_TMEM_COLS);
+  }
 }
 
 fea_status launch(const AsmArgs<float>& a, cudaStream_t s) {
-  const H27Layout L(a.eq_count);
+  // the tensor-core products serve the assembly (atomic or gather scatter), not the residual
+  const int tcp = a.resid ? 0 : a.contraction == FEA_CONTRACT_TC_BF16X3 ? 2 : a.contraction == FEA_CONTRACT_TC_TF32X3 ? 4 : 0;
+  const H27Layout L(a.eq_count, tcp);
   const size_t smem = sizeof(float) * (size_t)L.total;
   if (smem > 227 * 1024) return fail(FEA_ERR_TOO_LARGE, "hex27 kernel: shared memory");
-  auto kern = a.em ? k_hex27<true> : k_hex27<false>;
+  auto kern = tcp == 2 ? (a.em ? k_hex27<true, 2> : k_hex27<false, 2>)
+            : tcp == 4 ? (a.em ? k_hex27<true, 4> : k_hex27<false, 4>)
+                       : (a.em ? k_hex27<true, 0> : k_hex27<false, 0>);
   FEA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);

@@ -327,6 +327,7 @@ struct AsmArgs {
   double dt;
   double kappa_threshold;
   uint32_t* status;
+  int contraction = 0;  // Hex27 element matrices: fea_contraction (resolved: never AUTO here)
 };
 
 // Asynchronous global -> shared copies (4 bytes, or 16 bytes with both addresses 16-byte

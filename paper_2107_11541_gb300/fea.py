@@ -19,6 +19,7 @@ FEA_TET4, FEA_HEX8, FEA_HEX27, FEA_PEN6, FEA_PYR5 = 0, 1, 2, 3, 4
 FEA_F64_PLAIN, FEA_F32_FUSED = 0, 1
 FEA_TERM_MASS, FEA_TERM_CONV, FEA_TERM_DIFF, FEA_TERM_REAC, FEA_TERM_SUPG, FEA_TERM_ALL = 1, 2, 4, 8, 16, 31
 FEA_SCATTER_AUTO, FEA_SCATTER_ATOMIC, FEA_SCATTER_ROWOWNED, FEA_SCATTER_GATHER = 0, 1, 2, 3
+FEA_CONTRACT_AUTO, FEA_CONTRACT_CUDA, FEA_CONTRACT_TC_BF16X3, FEA_CONTRACT_TC_TF32X3 = 0, 1, 2, 3
 STATUS = {0: "FEA_OK", 1: "FEA_ERR_ARG", 2: "FEA_ERR_RANGE", 3: "FEA_ERR_DUP_NODE", 4: "FEA_ERR_INVERTED",
           5: "FEA_ERR_TOO_LARGE", 6: "FEA_ERR_OOM", 7: "FEA_ERR_CUDA", 8: "FEA_ERR_TIMEOUT", 9: "FEA_ERR_STATE"}
 NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27, FEA_PEN6: 6, FEA_PYR5: 5}
@@ -43,7 +44,7 @@ class fea_assemble_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("terms", C.c_int32), ("scatter", C.c_int32), ("accumulate", C.c_int32),
                 ("kappa_threshold", C.c_double), ("event_begin", C.c_void_p), ("event_end", C.c_void_p),
                 ("eq_groups", C.c_int32), ("cancel_check", C.c_int32), ("host_parts", C.c_int32),
-                ("reserved", C.c_int32 * 1)]
+                ("contraction", C.c_int32)]
 
 
 _lib = None
