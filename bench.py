@@ -325,6 +325,17 @@ def aggregate_over_ranks(ms, kernel_ms, units_per_rank, world, dist, device):
     return ms, kernel_ms, units_per_rank * world / (ms * 1e-3)
 
 
+def tuned_dict(tc: dict) -> dict:
+    """The autotuned configuration (fea_tuned_config) in words."""
+    return {"scatter": {1: "atomic", 2: "rowowned", 3: "gather"}.get(tc["scatter"], str(tc["scatter"])),
+            "eq_groups": tc["eq_groups"],
+            "mapping": {1: "type kernel", 2: "warp per element"}.get(tc["mapping"], str(tc["mapping"])),
+            "elems_per_cta": tc["elems_per_cta"] or "rule",
+            "contraction": {1: "cuda cores", 2: "tensor cores bf16x3", 3: "tensor cores 3xtf32"}.get(
+                tc["contraction"], str(tc["contraction"])),
+            "tuning_from_cache": bool(tc["from_cache"])}
+
+
 def config_dict(workload, w, nnz):
     m = w.mesh
     return {"workload": workload, "elem_type": G.NAMES[m.elem_type], "elements": m.n_elem, "nodes": m.n_node,
@@ -482,9 +493,8 @@ def main():
            "clocks": clk, "gpu_launches": int(launches), "kernel_ms": kernel_ms, "roofline": roof,
            "roofline_other": other}
     try:
-        sc, gr = fea.fea_tuned_strategy(p, q)
-        out["config"]["scatter"] = {1: "atomic", 2: "rowowned", 3: "gather"}.get(sc, str(sc))
-        out["config"]["eq_groups"] = gr
+        tc = fea.fea_tuned_config(p, q)
+        out["config"].update(tuned_dict(tc))
     except fea.FeaError:
         out["config"]["scatter"] = {0: "auto", 1: "atomic", 2: "rowowned", 3: "gather"}[args.scatter]
     if args.graph:
@@ -564,8 +574,7 @@ def main():
         out["laplacian"] = {"ms": lms, "value": m.n_elem / (lms * 1e-3), "unit": "elements/s",
                             "what": "K = sum_e int grad N_a . grad N_b (DIFF term, k = 1), FP32, one equation"}
         try:
-            sc, _ = fea.fea_tuned_strategy(p, 1)
-            out["laplacian"]["scatter"] = {1: "atomic", 2: "rowowned", 3: "gather"}.get(sc, str(sc))
+            out["laplacian"].update(tuned_dict(fea.fea_tuned_config(p, 1, fea.FEA_TERM_DIFF)))
         except fea.FeaError:
             pass
         if rank == 0 and not args.no_parity:
@@ -684,9 +693,7 @@ def side_workload(name: str, steps: int, warmup: int, parity: bool):
            "value": m.n_elem * q / (kernel_ms * 1e-3), "unit": UNIT, "roofline": roof, "roofline_other": other,
            "clocks": clk}
     try:
-        sc, gr = fea.fea_tuned_strategy(p, q)
-        res["config"]["scatter"] = {1: "atomic", 2: "rowowned", 3: "gather"}.get(sc, str(sc))
-        res["config"]["eq_groups"] = gr
+        res["config"].update(tuned_dict(fea.fea_tuned_config(p, q)))
     except fea.FeaError:
         pass
     if parity:

@@ -96,11 +96,14 @@ enum {
 };
 
 typedef enum {
-  FEA_SCATTER_AUTO = 0,     /* autotuned: the first FP32 call for a pattern and equation count times
-                               the candidates (row-owned with 1-4 equation groups where available,
-                               gather, atomic; skipping those too large to try) and keeps the fastest.
-                               Not tuned while the stream is capturing or with accumulate = 1: then
-                               row-owned if available, else atomic */
+  FEA_SCATTER_AUTO = 0,     /* autotuned: the first FP32 call for a pattern, equation count and term mask
+                               times the candidates of fea_tune_candidates (scatter x equation groups x
+                               Gauss-point mapping x elements per CTA x Hex27 contraction; those too
+                               large to try are skipped; row-owned batch sizes are tried for the best
+                               group count only) and keeps the fastest; the choice is also stored in and
+                               read back from the tuning cache file (see fea_tuned_config).  Not tuned
+                               while the stream is capturing or with accumulate = 1: then row-owned if
+                               available, else atomic, with the type kernels */
   FEA_SCATTER_ATOMIC = 1,   /* element-parallel, atomic adds into zeroed outputs */
   FEA_SCATTER_ROWOWNED = 2, /* rows accumulated in shared memory and written once (deterministic) */
   FEA_SCATTER_GATHER = 3    /* FP32 only: element matrices to a device scratch buffer owned by the pattern,
@@ -117,6 +120,16 @@ typedef enum {
                                  cleared, and the exact remainder), the same three products (about 22
                                  bits of each operand), FP32 accumulation */
 } fea_contraction;
+
+typedef enum {
+  FEA_MAP_AUTO = 0,             /* autotuned with the scatter (see FEA_SCATTER_AUTO); else FEA_MAP_TYPE_KERNEL */
+  FEA_MAP_TYPE_KERNEL = 1,      /* the kernel specialised for the element type: one thread per (element,
+                                   equation) walking the Gauss points (Tet4, Pen6, Pyr5; batched for Hex8,
+                                   with one thread per (element, Gauss point) for the shared geometry), or one
+                                   CTA per element with threads over (Gauss point, node) tasks (Hex27) */
+  FEA_MAP_WARP_PER_ELEMENT = 2  /* one warp per element, any type: lanes over the Gauss points for the
+                                   geometry, then over the matrix entries */
+} fea_mapping;
 
 typedef struct {
   int32_t precision;        /* fea_precision, default FEA_F32_FUSED */
@@ -140,7 +153,25 @@ typedef struct {
   int32_t contraction;      /* fea_contraction: how the FP32 Hex27 element matrices (full operator, up to
                                12 equations) are contracted; other element types and the residual use
                                the CUDA cores.  Default FEA_CONTRACT_AUTO */
+  int32_t mapping;          /* fea_mapping: Gauss-point-to-thread mapping of the FP32 element kernels
+                               (atomic and gather scatters, residual).  Default FEA_MAP_AUTO */
+  int32_t elems_per_cta;    /* FP32 work per CTA, 0 = the kernel's own rule (default): elements per batch
+                               of the Hex8 kernels (row-owned: 1-32, element-parallel: 1-96); threads per
+                               CTA, one (element, equation) each, of the Tet4 (128 or 256) and Pen6/Pyr5
+                               (64 or 128) kernels; ignored elsewhere */
+  int32_t reserved[2];
 } fea_assemble_opts;
+
+/* One autotuned configuration (fea_tuned_config, fea_tune_candidates). */
+typedef struct {
+  int32_t scatter;          /* fea_scatter */
+  int32_t eq_groups;        /* equation groups (row-owned scatter), else 1 */
+  int32_t mapping;          /* fea_mapping */
+  int32_t elems_per_cta;    /* 0 = the kernel's rule */
+  int32_t contraction;      /* fea_contraction */
+  int32_t from_cache;       /* 1 when taken from the tuning cache file instead of timed in this process */
+  float ms;                 /* the timed assembly, ms (as recorded in the cache when from_cache = 1) */
+} fea_tuning;
 
 /* Fills *opts with the defaults listed above. */
 FEA_API fea_status fea_default_opts(fea_assemble_opts* opts);
@@ -335,10 +366,33 @@ FEA_API fea_status fea_pcg(const fea_pattern* pattern, const float* values, cons
 
 /*
  * fea_tuned_strategy -- the scatter (fea_scatter) and equation-group count that
- * FEA_SCATTER_AUTO settled on for this pattern and n_eq.  FEA_ERR_STATE if no FP32
- * FEA_SCATTER_AUTO call has tuned that equation count yet.  Host only; does not wait.
+ * FEA_SCATTER_AUTO settled on for this pattern and n_eq (full operator).  FEA_ERR_STATE if no
+ * FP32 FEA_SCATTER_AUTO call has tuned that equation count yet.  Host only; does not wait.
  */
 FEA_API fea_status fea_tuned_strategy(const fea_pattern* pattern, int32_t n_eq, int32_t* scatter, int32_t* eq_groups);
+
+/*
+ * fea_tuned_config -- every dimension FEA_SCATTER_AUTO settled on for this pattern, n_eq and
+ * term mask (terms: FEA_TERM_* bits as passed in opts).  FEA_ERR_STATE before the first such
+ * call.  Host only; does not wait.
+ * The tuning cache: a JSON file, one object whose keys name the GPU, the element type (or
+ * "mixed"), n_eq, the term mask and the mesh size class (element and node counts rounded to
+ * powers of two), each mapped to a fea_tuning.  Its path is the environment variable
+ * FEA_TUNE_CACHE, else $XDG_CACHE_HOME/fea_gb300/tuning.json, else
+ * $HOME/.cache/fea_gb300/tuning.json; FEA_TUNE_CACHE=off disables it.  A tuned choice is
+ * merged into the file (written to a temporary file, then renamed); a later process that
+ * meets the same key uses the stored choice without timing.  A file that cannot be read or
+ * written is ignored.
+ */
+FEA_API fea_status fea_tuned_config(const fea_pattern* pattern, int32_t n_eq, int32_t terms, fea_tuning* out);
+
+/*
+ * fea_tune_candidates -- the configurations FEA_SCATTER_AUTO may time for this pattern, n_eq
+ * and term mask (every one is a valid explicit setting of opts): up to cap of them into out
+ * (host array), their number in *count.  Host only; builds no schedule and launches nothing.
+ */
+FEA_API fea_status fea_tune_candidates(const fea_pattern* pattern, int32_t n_eq, int32_t terms, fea_tuning* out,
+                                       int32_t cap, int32_t* count);
 
 /*
  * fea_cancel_rows -- the cancellation check (opts.cancel_check = 1, FP32 path).  Row i of an

@@ -2,9 +2,13 @@
 // build on the device (Sec. 4.2: CSR storage of the assembled matrix).
 #include <cuda_runtime.h>
 
+#include <sys/stat.h>
+#include <unistd.h>
+
 #include <algorithm>
 #include <atomic>
 #include <climits>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -378,6 +382,8 @@ static fea_status check_assemble_args(fea_mesh* m, const fea_pattern* p, const v
   if (o->host_parts < 0) return fail(FEA_ERR_ARG, "host_parts must be >= 0");
   if (o->contraction < FEA_CONTRACT_AUTO || o->contraction > FEA_CONTRACT_TC_TF32X3)
     return fail(FEA_ERR_ARG, "unknown contraction");
+  if (o->mapping < FEA_MAP_AUTO || o->mapping > FEA_MAP_WARP_PER_ELEMENT) return fail(FEA_ERR_ARG, "unknown mapping");
+  if (o->elems_per_cta < 0 || o->elems_per_cta > 256) return fail(FEA_ERR_ARG, "elems_per_cta must be in [0, 256]");
   if (m->mixed && (o->scatter == FEA_SCATTER_ROWOWNED || o->scatter == FEA_SCATTER_GATHER || o->cancel_check))
     return fail(FEA_ERR_ARG, "a mesh of several element types scatters with atomics (no row-owned, gather or "
                              "cancellation check)");
@@ -428,6 +434,8 @@ static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, 
   a.status = m->status;
   a.elem_order = (!m->mixed && m->type == FEA_TET4) ? p->elem_order : nullptr;
   a.contraction = o->contraction == FEA_CONTRACT_AUTO ? FEA_CONTRACT_CUDA : o->contraction;
+  a.mapping = o->mapping == FEA_MAP_AUTO ? FEA_MAP_TYPE_KERNEL : o->mapping;
+  a.batch = o->elems_per_cta;
   return a;
 }
 
@@ -437,22 +445,35 @@ static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, 
 
 namespace {
 
+// One complete choice of how an FP32 assembly runs (a fea_tuning without the bookkeeping).
 struct Strategy {
-  int scatter;  // fea_scatter, never AUTO here except before resolution
-  int groups;   // equation groups of the row-owned scatter
+  int scatter;      // fea_scatter, never AUTO here except before resolution
+  int groups;       // equation groups of the row-owned scatter
+  int mapping;      // fea_mapping (TYPE_KERNEL or WARP_PER_ELEMENT)
+  int batch;        // elements_per_cta, 0 = the kernel's rule
+  int contraction;  // fea_contraction (CUDA or a tensor-core variant)
 };
+
+Strategy from_tuning(const fea_tuning& t) { return Strategy{t.scatter, t.eq_groups, t.mapping, t.elems_per_cta, t.contraction}; }
+fea_tuning to_tuning(const Strategy& s, int from_cache, float ms) {
+  return fea_tuning{s.scatter, s.groups, s.mapping, s.batch, s.contraction, from_cache, ms};
+}
 
 // FP32 element-parallel launch over every element block: the batched Hex8 kernel for Hex8
 // blocks (its node-major field scratch held by the plan of a single-type mesh, else by the
-// pattern), the per-type kernels behind launch_generic_f32 for the others.
+// pattern), the per-type kernels behind launch_generic_f32 for the others; with the
+// warp-per-element mapping the generic kernel for every block.
 fea_status elem_f32(fea_mesh* m, fea_pattern* p, const AsmArgs<float>& a0, cudaStream_t s) {
   for (const fea_mesh::Block& b : m->blocks) {
     if (b.n_elem == 0) continue;
     AsmArgs<float> a = a0;
     set_block(a, b, p);
-    if (b.type == FEA_HEX8 && p->plan) FEA_TRY(plan_elem(p->plan, a, s));
-    else if (b.type == FEA_HEX8) FEA_TRY(hex8_elem(p->hex8_fnode, p->hex8_fnode_bytes, a, s));
-    else FEA_TRY(launch_generic_f32(a, b.type, s));
+    if (b.type == FEA_HEX8 && a.mapping != FEA_MAP_WARP_PER_ELEMENT) {
+      if (p->plan) FEA_TRY(plan_elem(p->plan, a, s));
+      else FEA_TRY(hex8_elem(p->hex8_fnode, p->hex8_fnode_bytes, a, s));
+    } else {
+      FEA_TRY(launch_generic_f32(a, b.type, s));
+    }
   }
   return FEA_OK;
 }
@@ -486,7 +507,7 @@ fea_status run_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const void
   const bool f32 = o.precision == FEA_F32_FUSED;
   bool rowowned = false;
   if (f32 && (st.scatter == FEA_SCATTER_ROWOWNED || st.scatter == FEA_SCATTER_AUTO)) {
-    FEA_TRY(plan_prepare(p->plan, plan_group_size(n_eq, st.groups), &rowowned));
+    FEA_TRY(plan_prepare(p->plan, plan_group_size(n_eq, st.groups), st.batch, &rowowned));
     if (st.scatter == FEA_SCATTER_ROWOWNED && !rowowned)
       return fail(FEA_ERR_ARG, "row-owned scatter is not available for this mesh type, precision or equation count");
   }
@@ -517,6 +538,9 @@ fea_status run_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const void
       FEA_TRY(elem_f64(m, p, a, n_eq, s));
     } else {
       AsmArgs<float> a = make_args<float>(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs);
+      a.mapping = st.mapping;
+      a.batch = st.batch;
+      a.contraction = st.contraction;
       if (rowowned) {
         FEA_TRY(plan_assemble(p->plan, a, o.accumulate, st.groups, s));
       } else if (gather) {
@@ -532,46 +556,196 @@ fea_status run_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const void
   return FEA_OK;
 }
 
-// Resolves FEA_SCATTER_AUTO for an FP32 call.  The first call for a pattern and equation
-// count times every candidate on the caller's own inputs (each result overwrites values and
-// rhs, so the outputs end up assembled whichever ran last) and caches the fastest.
+// The strategy an explicit (non-AUTO) opts asks for.
+Strategy explicit_strategy(const fea_assemble_opts& o) {
+  return Strategy{o.scatter, std::max(1, o.eq_groups), o.mapping == FEA_MAP_AUTO ? (int)FEA_MAP_TYPE_KERNEL : o.mapping,
+                  o.elems_per_cta, o.contraction == FEA_CONTRACT_AUTO ? (int)FEA_CONTRACT_CUDA : o.contraction};
+}
+
+const char* type_name(const fea_mesh* m) {
+  if (m->mixed) return "mixed";
+  switch (m->type) {
+    case FEA_TET4: return "tet4";
+    case FEA_HEX8: return "hex8";
+    case FEA_HEX27: return "hex27";
+    case FEA_PEN6: return "pen6";
+    case FEA_PYR5: return "pyr5";
+  }
+  return "unknown";
+}
+
+// The candidates of FEA_SCATTER_AUTO, in the order they are timed.  Row-owned schedules with
+// batch sizes other than the kernel's rule are listed for every group count here; the tuner
+// times them for the best group count only.
+std::vector<Strategy> candidates(fea_mesh* m, fea_pattern* p, int32_t n_eq, int terms) {
+  std::vector<Strategy> c;
+  const int T = FEA_MAP_TYPE_KERNEL, W = FEA_MAP_WARP_PER_ELEMENT, CU = FEA_CONTRACT_CUDA;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const bool gather_fits = !m->mixed && gather_scratch_bytes(m->n_elem, m->nen, n_eq) <= free_b / 2;
+  // atomics into DRAM run at a few G/s, and the warp-per-element kernel is several times slower
+  // than the type kernels: time them only where a trial stays short
+  const double work = (double)m->n_elem * m->nen * m->nen * n_eq;
+  const bool short_trial = work < 2e9;
+  if (m->mixed) {
+    c.push_back(Strategy{FEA_SCATTER_ATOMIC, 1, T, 0, CU});
+    if (short_trial) c.push_back(Strategy{FEA_SCATTER_ATOMIC, 1, W, 0, CU});
+    return c;
+  }
+  if (p->plan) {  // Hex8: row-owned schedules per group count, then batch sizes
+    int last = -1;
+    for (int g = 1; g <= 4 && g <= n_eq; ++g) {
+      const int size = plan_group_size(n_eq, g);
+      if (size == last) continue;
+      last = size;
+      c.push_back(Strategy{FEA_SCATTER_ROWOWNED, g, T, 0, CU});
+      for (int be : {16, 32}) c.push_back(Strategy{FEA_SCATTER_ROWOWNED, g, T, be, CU});
+    }
+  }
+  std::vector<int> batches{0};
+  if (m->type == FEA_HEX8) batches = {0, 32};
+  if (m->type == FEA_TET4) batches = {0, 128};
+  if (m->type == FEA_PEN6 || m->type == FEA_PYR5) batches = {0, 64};
+  std::vector<int> contractions{CU};
+  if (m->type == FEA_HEX27 && terms == FEA_TERM_ALL && n_eq <= 12) contractions.push_back(FEA_CONTRACT_TC_TF32X3);
+  for (int sc : {(int)FEA_SCATTER_GATHER, (int)FEA_SCATTER_ATOMIC}) {
+    if (sc == FEA_SCATTER_GATHER && !gather_fits) continue;
+    if (sc == FEA_SCATTER_ATOMIC && !short_trial && !c.empty()) continue;
+    for (int be : batches)
+      for (int ct : contractions) c.push_back(Strategy{sc, 1, T, be, ct});
+    if (short_trial) c.push_back(Strategy{sc, 1, W, 0, CU});
+  }
+  if (c.empty()) c.push_back(Strategy{FEA_SCATTER_ATOMIC, 1, T, 0, CU});
+  return c;
+}
+
+// ---- the tuning cache file
+
+std::string cache_path() {
+  const char* e = getenv("FEA_TUNE_CACHE");
+  if (e) return (strcmp(e, "off") == 0 || !*e) ? std::string() : std::string(e);
+  const char* x = getenv("XDG_CACHE_HOME");
+  if (x && *x) return std::string(x) + "/fea_gb300/tuning.json";
+  const char* h = getenv("HOME");
+  if (h && *h) return std::string(h) + "/.cache/fea_gb300/tuning.json";
+  return std::string();
+}
+
+std::string cache_key(fea_mesh* m, int32_t n_eq, int terms) {
+  cudaDeviceProp prop;
+  std::string gpu = cudaGetDeviceProperties(&prop, m->device) == cudaSuccess ? prop.name : "gpu";
+  for (char& ch : gpu)
+    if (ch == '"' || ch == '\\') ch = '_';
+  auto log2r = [](int64_t n) { return n <= 1 ? 0 : (int)std::lround(std::log2((double)n)); };
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s|%s|q%d|t%d|f32|E2^%d|N2^%d", gpu.c_str(), type_name(m), n_eq, terms,
+           log2r(m->n_elem), log2r(m->n_node));
+  return buf;
+}
+
+// The file is one JSON object of "key": {"scatter": s, "eq_groups": g, "mapping": m,
+// "elems_per_cta": b, "contraction": c, "ms": t} entries, one per line (as written below).
+std::map<std::string, fea_tuning> cache_read(const std::string& path) {
+  std::map<std::string, fea_tuning> out;
+  FILE* f = path.empty() ? nullptr : fopen(path.c_str(), "r");
+  if (!f) return out;
+  char line[1024];
+  while (fgets(line, sizeof line, f)) {
+    const char* q0 = strchr(line, '"');
+    const char* q1 = q0 ? strchr(q0 + 1, '"') : nullptr;
+    if (!q1) continue;
+    fea_tuning t{};
+    int sc, g, mp, be, ct;
+    float ms;
+    if (sscanf(q1 + 1, " : {\"scatter\": %d, \"eq_groups\": %d, \"mapping\": %d, \"elems_per_cta\": %d, "
+                       "\"contraction\": %d, \"ms\": %f}", &sc, &g, &mp, &be, &ct, &ms) != 6)
+      continue;
+    t.scatter = sc;
+    t.eq_groups = g;
+    t.mapping = mp;
+    t.elems_per_cta = be;
+    t.contraction = ct;
+    t.ms = ms;
+    out[std::string(q0 + 1, q1)] = t;
+  }
+  fclose(f);
+  return out;
+}
+
+void cache_write(const std::string& path, const std::string& key, const fea_tuning& t) {
+  if (path.empty()) return;
+  std::map<std::string, fea_tuning> all = cache_read(path);
+  all[key] = t;
+  const size_t slash = path.find_last_of('/');
+  if (slash != std::string::npos) {  // create the directories (mkdir -p), ignoring failures
+    for (size_t i = 1; i <= slash; ++i)
+      if (path[i] == '/' || i == slash) {
+        const std::string d = path.substr(0, i == slash ? slash : i);
+        if (!d.empty()) mkdir(d.c_str(), 0755);
+      }
+  }
+  const std::string tmp = path + "." + std::to_string((long long)getpid()) + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return;
+  fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : all) {
+    const fea_tuning& v = kv.second;
+    fprintf(f, " \"%s\": {\"scatter\": %d, \"eq_groups\": %d, \"mapping\": %d, \"elems_per_cta\": %d, "
+               "\"contraction\": %d, \"ms\": %.4f}%s\n", kv.first.c_str(), v.scatter, v.eq_groups, v.mapping,
+            v.elems_per_cta, v.contraction, v.ms, ++i < all.size() ? "," : "");
+  }
+  fprintf(f, "}\n");
+  const bool ok = fclose(f) == 0;
+  if (ok) rename(tmp.c_str(), path.c_str());
+  else remove(tmp.c_str());
+}
+
+// Whether a cached strategy still applies to this pattern (the row-owned schedule builds).
+bool strategy_valid(fea_mesh* m, fea_pattern* p, int32_t n_eq, int terms, const Strategy& st) {
+  for (const Strategy& c : candidates(m, p, n_eq, terms))
+    if (c.scatter == st.scatter && c.groups == st.groups && c.mapping == st.mapping && c.batch == st.batch &&
+        c.contraction == st.contraction) {
+      if (st.scatter != FEA_SCATTER_ROWOWNED) return true;
+      bool ok = false;
+      return plan_prepare(p->plan, plan_group_size(n_eq, st.groups), st.batch, &ok) == FEA_OK && ok;
+    }
+  return false;
+}
+
+// Resolves FEA_SCATTER_AUTO for an FP32 call.  The first call for a pattern, equation count
+// and term mask takes the choice from the tuning cache file, or else times the candidates on
+// the caller's own inputs (each result overwrites values and rhs, so the outputs end up
+// assembled whichever ran last), keeps the fastest and records it in the file.
 fea_status choose_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const void* kd, const void* sr,
                            const void* phi, double dt, int32_t n_eq, const fea_assemble_opts& o, void* values,
                            void* rhs, Strategy* out) {
-  auto it = p->tuned.find(n_eq);
+  const std::pair<int, int> tkey(n_eq, o.terms);
+  auto it = p->tuned.find(tkey);
   if (it != p->tuned.end()) {
-    *out = Strategy{it->second.first, it->second.second};
-    return FEA_OK;
-  }
-  if (m->mixed) {  // several element types: atomics only
-    p->tuned[n_eq] = std::make_pair((int)FEA_SCATTER_ATOMIC, 1);
-    *out = Strategy{FEA_SCATTER_ATOMIC, 1};
+    *out = from_tuning(it->second);
     return FEA_OK;
   }
   bool ro1 = false;
-  FEA_TRY(plan_prepare(p->plan, n_eq, &ro1));
-  const Strategy fallback{ro1 ? FEA_SCATTER_ROWOWNED : FEA_SCATTER_ATOMIC, 1};
+  FEA_TRY(plan_prepare(p->plan, n_eq, 0, &ro1));
+  const Strategy fallback{ro1 ? FEA_SCATTER_ROWOWNED : FEA_SCATTER_ATOMIC, 1, FEA_MAP_TYPE_KERNEL, 0, FEA_CONTRACT_CUDA};
   if (o.accumulate || m->n_elem == 0 || stream_capturing(m->stream)) {  // cannot run trials
     *out = fallback;
     return FEA_OK;
   }
-  std::vector<Strategy> cand;
-  int last_size = -1;
-  for (int g = 1; g <= 4 && g <= n_eq; ++g) {
-    const int size = plan_group_size(n_eq, g);
-    if (size == last_size) continue;
-    last_size = size;
-    bool ok = false;
-    FEA_TRY(plan_prepare(p->plan, size, &ok));
-    if (ok) cand.push_back(Strategy{FEA_SCATTER_ROWOWNED, g});
+  const std::string path = cache_path(), key = cache_key(m, n_eq, o.terms);
+  {
+    const std::map<std::string, fea_tuning> cached = cache_read(path);
+    auto ci = cached.find(key);
+    if (ci != cached.end() && strategy_valid(m, p, n_eq, o.terms, from_tuning(ci->second))) {
+      fea_tuning t = ci->second;
+      t.from_cache = 1;
+      p->tuned[tkey] = t;
+      *out = from_tuning(t);
+      return FEA_OK;
+    }
   }
-  size_t free_b = 0, total_b = 0;
-  cudaMemGetInfo(&free_b, &total_b);
-  if (gather_scratch_bytes(m->n_elem, m->nen, n_eq) <= free_b / 2) cand.push_back(Strategy{FEA_SCATTER_GATHER, 1});
-  // atomics into DRAM run at a few G/s: try them only where a trial stays short
-  if ((double)m->n_elem * m->nen * m->nen * n_eq < 2e9 || cand.empty())
-    cand.push_back(Strategy{FEA_SCATTER_ATOMIC, 1});
-
+  const std::vector<Strategy> all = candidates(m, p, n_eq, o.terms);
   fea_assemble_opts oq = o;
   oq.event_begin = oq.event_end = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -580,7 +754,12 @@ fea_status choose_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const v
   Strategy best = fallback;
   float best_ms = 0.f;
   fea_status status = FEA_OK;
-  for (const Strategy& c : cand) {
+  auto time_one = [&](const Strategy& c) -> fea_status {
+    if (c.scatter == FEA_SCATTER_ROWOWNED) {
+      bool ok = false;
+      FEA_TRY(plan_prepare(p->plan, plan_group_size(n_eq, c.groups), c.batch, &ok));
+      if (!ok) return FEA_OK;  // no schedule for this group size or batch: not a candidate
+    }
     float ms = 0.f;
     fea_status s1 = run_strategy(m, p, vel, kd, sr, phi, dt, n_eq, oq, values, rhs, c);  // warm-up
     if (s1 == FEA_OK) s1 = fea_sync(m);
@@ -589,27 +768,41 @@ fea_status choose_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const v
     if (s1 == FEA_OK && cudaEventRecord(e1, m->stream) != cudaSuccess) s1 = FEA_ERR_CUDA;
     if (s1 == FEA_OK) s1 = fea_sync(m);
     if (s1 == FEA_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) s1 = FEA_ERR_CUDA;
-    if (s1 == FEA_ERR_OOM || s1 == FEA_ERR_TOO_LARGE) continue;  // a candidate that does not fit is skipped
-    if (s1 != FEA_OK) {
-      status = s1;
-      break;
-    }
+    if (s1 == FEA_ERR_OOM || s1 == FEA_ERR_TOO_LARGE) return FEA_OK;  // a candidate that does not fit is skipped
+    if (s1 != FEA_OK) return s1;
     if (best_ms == 0.f || ms < best_ms) {
       best_ms = ms;
       best = c;
     }
+    return FEA_OK;
+  };
+  // stage 1: every candidate with the kernels' own batch rule (and every non-row-owned one)
+  for (const Strategy& c : all) {
+    if (c.scatter == FEA_SCATTER_ROWOWNED && c.batch != 0) continue;
+    if ((status = time_one(c)) != FEA_OK) break;
+  }
+  // stage 2: the row-owned batch sizes, for the best group count only
+  if (status == FEA_OK && best.scatter == FEA_SCATTER_ROWOWNED) {
+    const int g = best.groups;
+    for (const Strategy& c : all)
+      if (c.scatter == FEA_SCATTER_ROWOWNED && c.batch != 0 && c.groups == g)
+        if ((status = time_one(c)) != FEA_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (status != FEA_OK) return status;
-  // keep the resources of the winners (this equation count's and those tuned before) only
-  p->tuned[n_eq] = std::make_pair(best.scatter, best.groups);
+  const fea_tuning t = to_tuning(best, 0, best_ms);
+  p->tuned[tkey] = t;
+  cache_write(path, key, t);
+  // keep the resources of the winners (this call's and those tuned before) only
   std::vector<int> keep;
   bool any_gather = false;
   for (const auto& kv : p->tuned) {
-    if (kv.second.first == FEA_SCATTER_ROWOWNED) keep.push_back(plan_group_size(kv.first, kv.second.second));
-    any_gather |= kv.second.first == FEA_SCATTER_GATHER;
+    if (kv.second.scatter == FEA_SCATTER_ROWOWNED)
+      keep.push_back(plan_key(plan_group_size(kv.first.first, kv.second.eq_groups), kv.second.elems_per_cta));
+    any_gather |= kv.second.scatter == FEA_SCATTER_GATHER;
   }
+  keep.push_back(plan_key(n_eq, 0));  // the fallback schedule (stream capture, accumulate)
   plan_trim(p->plan, keep);
   if (!any_gather) {
     cudaFree(p->em);
@@ -959,7 +1152,7 @@ fea_status fea_assemble(fea_mesh* m, const fea_pattern* p, const void* vel, cons
   else fea_default_opts(&o);
   FEA_TRY(check_assemble_args(m, p, vel, kd, sr, phi, dt, n_eq, &o, values, rhs));
   fea_pattern* pw = const_cast<fea_pattern*>(p);  // schedules, scratch and the tuning cache belong to the pattern
-  Strategy st{o.scatter, std::max(1, o.eq_groups)};
+  Strategy st = explicit_strategy(o);
   if (o.precision == FEA_F32_FUSED && o.scatter == FEA_SCATTER_AUTO)
     FEA_TRY(choose_strategy(m, pw, vel, kd, sr, phi, dt, n_eq, o, values, rhs, &st));
   const bool check = o.cancel_check && o.precision == FEA_F32_FUSED && m->n_elem > 0;
@@ -1033,10 +1226,28 @@ fea_status fea_cancel_rows(const fea_pattern* p, int32_t n_eq, int64_t* count) {
 
 fea_status fea_tuned_strategy(const fea_pattern* p, int32_t n_eq, int32_t* scatter, int32_t* eq_groups) {
   if (!p || !scatter || !eq_groups) return fail(FEA_ERR_ARG, "fea_tuned_strategy: null argument");
-  auto it = p->tuned.find(n_eq);
+  auto it = p->tuned.find(std::make_pair((int)n_eq, (int)FEA_TERM_ALL));
   if (it == p->tuned.end()) return fail(FEA_ERR_STATE, "no tuned strategy for %d equations yet", n_eq);
-  *scatter = it->second.first;
-  *eq_groups = it->second.second;
+  *scatter = it->second.scatter;
+  *eq_groups = it->second.eq_groups;
+  return FEA_OK;
+}
+
+fea_status fea_tuned_config(const fea_pattern* p, int32_t n_eq, int32_t terms, fea_tuning* out) {
+  if (!p || !out) return fail(FEA_ERR_ARG, "fea_tuned_config: null argument");
+  auto it = p->tuned.find(std::make_pair((int)n_eq, (int)terms));
+  if (it == p->tuned.end()) return fail(FEA_ERR_STATE, "no tuned configuration for %d equations, terms %d", n_eq, terms);
+  *out = it->second;
+  return FEA_OK;
+}
+
+fea_status fea_tune_candidates(const fea_pattern* p, int32_t n_eq, int32_t terms, fea_tuning* out, int32_t cap,
+                               int32_t* count) {
+  if (!p || !count || (cap > 0 && !out) || n_eq <= 0) return fail(FEA_ERR_ARG, "fea_tune_candidates: bad argument");
+  fea_pattern* pw = const_cast<fea_pattern*>(p);
+  const std::vector<Strategy> c = candidates(pw->mesh, pw, n_eq, terms);
+  *count = (int32_t)c.size();
+  for (int i = 0; i < (int)c.size() && i < cap; ++i) out[i] = to_tuning(c[i], 0, 0.f);
   return FEA_OK;
 }
 

@@ -101,6 +101,7 @@ static fea_status launch_any(const AsmArgs<T>& a, fea_elem_t type, cudaStream_t 
 
 fea_status launch_generic_f64(const AsmArgs<double>& a, fea_elem_t type, cudaStream_t s) { return launch_any(a, type, s); }
 fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s) {
+  if (a.mapping == FEA_MAP_WARP_PER_ELEMENT) return launch_any(a, type, s);  // one warp per element
   if (type == FEA_TET4) return launch_tet4_f32(a, s);  // constant gradients: one thread per item
   if (type == FEA_PEN6 || type == FEA_PYR5) return launch_small_f32(a, type, s);  // one thread per item
   if (type == FEA_HEX27 && hex27_kernel_applies(a)) return launch_hex27_f32(a, s);  // one CTA per element

@@ -101,8 +101,8 @@ struct fea_pattern {
   // element-matrix scratch of the gather scatter, grown on demand
   void* em;
   size_t em_bytes;
-  // autotuned strategy per equation count: {scatter, equation groups}
-  std::map<int, std::pair<int, int>> tuned;
+  // autotuned configuration per (equation count, term mask)
+  std::map<std::pair<int, int>, fea_tuning> tuned;
   // cancellation check: the per-row flags every checked call recomputes ([n_node], shared by
   // all equation counts), and per equation count the device list of the rows the most recent
   // checked call flagged, with its device-side length
@@ -328,6 +328,8 @@ struct AsmArgs {
   double kappa_threshold;
   uint32_t* status;
   int contraction = 0;  // Hex27 element matrices: fea_contraction (resolved: never AUTO here)
+  int mapping = 1;      // fea_mapping (resolved: never AUTO here)
+  int batch = 0;        // elements per batch (Hex8 kernels) or threads per CTA (Tet4, Pen6, Pyr5); 0 = rule
 };
 
 // Asynchronous global -> shared copies (4 bytes, or 16 bytes with both addresses 16-byte

@@ -330,7 +330,7 @@ static fea_status host_copies(fea_rowowned_plan* P) {
   return FEA_OK;
 }
 
-static fea_status build_variant(fea_rowowned_plan* P, int n_eq, Variant* v) {
+static fea_status build_variant(fea_rowowned_plan* P, int n_eq, int batch, Variant* v) {
   FEA_TRY(host_copies(P));
   int64_t N = P->mesh->n_node, E = P->mesh->n_elem;
   int maxcol = 0;
@@ -344,7 +344,7 @@ static fea_status build_variant(fea_rowowned_plan* P, int n_eq, Variant* v) {
   v->maxcol = maxcol;
   v->row_stride = ((maxcol + 1) + 3) & ~3;  // slots start 16-byte aligned (bulk zeroing)
   v->unused_nodes = unused;
-  v->be = batch_elems(n_eq);
+  v->be = batch > 0 ? std::min(batch, BEMAX) : batch_elems(n_eq);
   size_t fixed = smem_fixed(v->be);
   if (fixed + 4096 > (size_t)SMEM_LIMIT) return FEA_OK;
   // per slot: its row of row_stride entries of neqs floats
@@ -452,20 +452,23 @@ void plan_destroy(fea_rowowned_plan* P) {
   delete P;
 }
 
-fea_status plan_prepare(fea_rowowned_plan* P, int n_eq, bool* ok) {
+int plan_key(int n_eq, int batch) { return n_eq | (std::max(0, std::min(batch, ro::BEMAX)) << 16); }
+
+fea_status plan_prepare(fea_rowowned_plan* P, int n_eq, int batch, bool* ok) {
   *ok = false;
   if (!P) return FEA_OK;
   std::lock_guard<std::mutex> lk(P->mu);
-  auto it = P->variants.find(n_eq);
+  const int key = plan_key(n_eq, batch);
+  auto it = P->variants.find(key);
   if (it == P->variants.end()) {
     ro::Variant* v = new (std::nothrow) ro::Variant();
     if (!v) return fail(FEA_ERR_OOM, "host allocation failed");
-    fea_status st = ro::build_variant(P, n_eq, v);
+    fea_status st = ro::build_variant(P, n_eq, batch, v);
     if (st != FEA_OK) {
       ro::free_variant(v);
       return st;
     }
-    it = P->variants.emplace(n_eq, v).first;
+    it = P->variants.emplace(key, v).first;
   }
   *ok = it->second->ok;
   return FEA_OK;
@@ -583,7 +586,7 @@ fea_status hex8_elem(float*& fnode, size_t& fnode_bytes, const AsmArgs<float>& a
   r.rec = rec;
   const bool full = a.terms == FEA_TERM_ALL;
   // 96 elements take 180 KB; the residual kernel of the full operator runs two CTAs per SM: 48
-  r.be = ro::elem_batch(a.eq_count, a.resid && full ? 48 : 96);
+  r.be = a.batch > 0 ? std::min(a.batch, 96) : ro::elem_batch(a.eq_count, a.resid && full ? 48 : 96);
   const size_t smem = sizeof(float) * (size_t)r.be * (ro::GEO_ELEM + ro::NEN * ro::RAW + ro::NEN);
   auto pick = [&](auto full_k, auto part_k) { return full ? full_k : part_k; };
   void (*kern)(ro::RoArgs) =
@@ -610,7 +613,7 @@ fea_status plan_elem(fea_rowowned_plan* P, const AsmArgs<float>& a, cudaStream_t
 
 fea_status plan_assemble(fea_rowowned_plan* P, const AsmArgs<float>& a, int accumulate, int groups, cudaStream_t s) {
   const int gsize = plan_group_size(a.eq_count, groups);
-  ro::Variant* v = P->variants.at(gsize);
+  ro::Variant* v = P->variants.at(plan_key(gsize, a.batch));
   if (v->unused_nodes && !accumulate)
     FEA_CUDA_TRY(cudaMemsetAsync(a.rhs + (int64_t)a.eq0 * a.n_node, 0,
                                  sizeof(float) * (size_t)a.eq_count * (size_t)a.n_node, s));

@@ -204,10 +204,11 @@ fea_status launch_t(const AsmArgs<float>& a, cudaStream_t s) {
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_f32<TYPE>, 128, 0);
+  const int threads = a.batch == 64 ? 64 : 128;  // one (element, equation) item per thread
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_f32<TYPE>, threads, 0);
   const int64_t cap = (int64_t)nsm * std::max(per_sm, 1) * 8;
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 127) / 128, cap));
-  k_small_f32<TYPE><<<grid, 128, 0, s>>>(a);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + threads - 1) / threads, cap));
+  k_small_f32<TYPE><<<grid, threads, 0, s>>>(a);
   FEA_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return FEA_OK;

@@ -180,8 +180,10 @@ fea_status launch_tet4_f32(const AsmArgs<float>& a, cudaStream_t s) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, (int64_t)nsm * 16));
-  k_tet4_f32<<<grid, 256, 0, s>>>(a);
+  const int threads = a.batch == 128 ? 128 : 256;  // one (element, equation) item per thread
+  const unsigned grid = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((items + threads - 1) / threads, (int64_t)nsm * 16 * (256 / threads)));
+  k_tet4_f32<<<grid, threads, 0, s>>>(a);
   FEA_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return FEA_OK;

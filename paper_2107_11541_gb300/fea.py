@@ -20,6 +20,7 @@ FEA_F64_PLAIN, FEA_F32_FUSED = 0, 1
 FEA_TERM_MASS, FEA_TERM_CONV, FEA_TERM_DIFF, FEA_TERM_REAC, FEA_TERM_SUPG, FEA_TERM_ALL = 1, 2, 4, 8, 16, 31
 FEA_SCATTER_AUTO, FEA_SCATTER_ATOMIC, FEA_SCATTER_ROWOWNED, FEA_SCATTER_GATHER = 0, 1, 2, 3
 FEA_CONTRACT_AUTO, FEA_CONTRACT_CUDA, FEA_CONTRACT_TC_BF16X3, FEA_CONTRACT_TC_TF32X3 = 0, 1, 2, 3
+FEA_MAP_AUTO, FEA_MAP_TYPE_KERNEL, FEA_MAP_WARP_PER_ELEMENT = 0, 1, 2
 STATUS = {0: "FEA_OK", 1: "FEA_ERR_ARG", 2: "FEA_ERR_RANGE", 3: "FEA_ERR_DUP_NODE", 4: "FEA_ERR_INVERTED",
           5: "FEA_ERR_TOO_LARGE", 6: "FEA_ERR_OOM", 7: "FEA_ERR_CUDA", 8: "FEA_ERR_TIMEOUT", 9: "FEA_ERR_STATE"}
 NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27, FEA_PEN6: 6, FEA_PYR5: 5}
@@ -29,7 +30,8 @@ EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_create_mixed", "fea_
            "fea_pattern_build", "fea_pattern_get", "fea_pattern_destroy", "fea_assemble", "fea_residual",
            "fea_assemble_host",
            "fea_pack_plan", "fea_csr_rowptr_noalloc", "fea_update_fields", "fea_graph_capture_steps",
-           "fea_graph_launch", "fea_graph_destroy", "fea_spmv", "fea_pcg", "fea_tuned_strategy", "fea_cancel_rows", "fea_last_error",
+           "fea_graph_launch", "fea_graph_destroy", "fea_spmv", "fea_pcg", "fea_tuned_strategy", "fea_tuned_config",
+           "fea_tune_candidates", "fea_cancel_rows", "fea_last_error",
            "fea_kernel_launches", "fea_version"]
 
 
@@ -44,7 +46,17 @@ class fea_assemble_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("terms", C.c_int32), ("scatter", C.c_int32), ("accumulate", C.c_int32),
                 ("kappa_threshold", C.c_double), ("event_begin", C.c_void_p), ("event_end", C.c_void_p),
                 ("eq_groups", C.c_int32), ("cancel_check", C.c_int32), ("host_parts", C.c_int32),
-                ("contraction", C.c_int32)]
+                ("contraction", C.c_int32), ("mapping", C.c_int32), ("elems_per_cta", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
+
+
+class fea_tuning(C.Structure):
+    _fields_ = [("scatter", C.c_int32), ("eq_groups", C.c_int32), ("mapping", C.c_int32),
+                ("elems_per_cta", C.c_int32), ("contraction", C.c_int32), ("from_cache", C.c_int32),
+                ("ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -78,6 +90,8 @@ def lib(path: str = LIB_PATH):
                                               vp, i32, C.POINTER(vp)]
         L.fea_graph_launch.argtypes = [vp]
         L.fea_tuned_strategy.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i32)]
+        L.fea_tuned_config.argtypes = [vp, i32, i32, C.POINTER(fea_tuning)]
+        L.fea_tune_candidates.argtypes = [vp, i32, i32, vp, i32, C.POINTER(i32)]
         L.fea_spmv.argtypes = [vp, vp, vp, vp, i32, i32, vp]
         L.fea_pcg.argtypes = [vp, vp, vp, vp, i32, i32, dbl, vp, vp, vp]
         L.fea_cancel_rows.argtypes = [vp, i32, C.POINTER(i64)]
@@ -260,6 +274,22 @@ def fea_tuned_strategy(pattern, n_eq: int):
     s, g = C.c_int32(), C.c_int32()
     _check(lib().fea_tuned_strategy(pattern, int(n_eq), C.byref(s), C.byref(g)))
     return s.value, g.value
+
+
+def fea_tuned_config(pattern, n_eq: int, terms: int = FEA_TERM_ALL) -> dict:
+    """Every dimension FEA_SCATTER_AUTO chose for this pattern, equation count and term mask."""
+    t = fea_tuning()
+    _check(lib().fea_tuned_config(pattern, int(n_eq), int(terms), C.byref(t)))
+    return t.as_dict()
+
+
+def fea_tune_candidates(pattern, n_eq: int, terms: int = FEA_TERM_ALL) -> list:
+    """The configurations FEA_SCATTER_AUTO may time, as dicts of fea_tuning fields."""
+    n = C.c_int32()
+    _check(lib().fea_tune_candidates(pattern, int(n_eq), int(terms), None, 0, C.byref(n)))
+    arr = (fea_tuning * max(1, n.value))()
+    _check(lib().fea_tune_candidates(pattern, int(n_eq), int(terms), arr, n.value, C.byref(n)))
+    return [arr[i].as_dict() for i in range(n.value)]
 
 
 def fea_cancel_rows(pattern, n_eq: int) -> int:

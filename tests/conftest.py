@@ -6,6 +6,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
+# the tests tune from scratch unless a test points the library at a cache file of its own
+os.environ["FEA_TUNE_CACHE"] = "off"
 
 
 def pytest_configure(config):

@@ -41,7 +41,8 @@ class GpuRun:
         return dev, dt
 
     def assemble(self, fields: G.Fields, precision: int, terms=fea.FEA_TERM_ALL, scatter=fea.FEA_SCATTER_AUTO,
-                 accumulate=0, out=None, eq_groups=0, cancel_check=0, contraction=fea.FEA_CONTRACT_AUTO):
+                 accumulate=0, out=None, eq_groups=0, cancel_check=0, contraction=fea.FEA_CONTRACT_AUTO,
+                 mapping=fea.FEA_MAP_AUTO, elems_per_cta=0):
         torch = self.torch
         (vel, kd, sr, phi), dt = self.upload(fields, precision)
         q = fields.n_eq
@@ -51,7 +52,8 @@ class GpuRun:
         else:
             values, rhs = out
         opts = fea.fea_default_opts(precision=precision, terms=terms, scatter=scatter, accumulate=accumulate,
-                                    eq_groups=eq_groups, cancel_check=cancel_check, contraction=contraction)
+                                    eq_groups=eq_groups, cancel_check=cancel_check, contraction=contraction,
+                                    mapping=mapping, elems_per_cta=elems_per_cta)
         fea.fea_assemble(self.handle, self.pattern, vel, kd, sr, phi, fields.dt, q, opts, values, rhs)
         fea.fea_sync(self.handle)
         return values, rhs
