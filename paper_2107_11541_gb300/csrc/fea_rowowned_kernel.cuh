@@ -102,81 +102,92 @@ __device__ __forceinline__ void stage_nodes(const RoArgs& r, int t, const Stage&
 }
 
 // Writes the rows completed by batch tb to HBM and clears their slots; warp w of nw takes a
-// contiguous share of the batch's records, which the plan sorts by row, so that a warp's
-// consecutive stores of one equation land on adjacent CSR rows.  Per row the lanes walk its
-// (equation, column) values with the column fastest (column index len is the RHS entry), so
-// each equation's segment is stored contiguously.  The warp reads 32 flush records at a
-// time, one per lane.
+// contiguous share of the batch's records, which the plan sorts by row.  Consecutive rows r,
+// r+1, ... have consecutive CSR ranges, so a run of them is one contiguous segment of every
+// equation's values (and of its RHS).  The warp reads 32 records at a time (one per lane),
+// splits them into runs, and writes each run per equation in chunks of 32 consecutive CSR
+// positions (one store instruction per chunk), each lane finding the row of its position by a
+// binary search over the run's records; the run's RHS entries are one store per equation.
+// The stores are plain: every value is written once.  Accumulating calls add row by row.
 __device__ __forceinline__ void flush_rows(const RoArgs& r, float* win, int tb, int w0, int nw) {
   const AsmArgs<float>& A_ = r.a;
   const int lane = threadIdx.x & 31, n_eq = A_.eq_count;
   const int fb = r.batch_flush[tb], nb = r.batch_flush[tb + 1] - fb;
   const int f0 = fb + (int)(((int64_t)nb * w0) / nw), nf = fb + (int)(((int64_t)nb * (w0 + 1)) / nw) - f0;
-  int4 rec = make_int4(0, 0, 0, 0);
-  for (int f = 0, j = 32; f < nf; ++f, ++j) {
-    if (j == 32) {  // records f .. f + 31
-      if (f + lane < nf) rec = __ldg(r.flush_meta + f0 + f + lane);
-      j = 0;
-    }
-    const int4 m = make_int4(__shfl_sync(0xffffffffu, rec.x, j), __shfl_sync(0xffffffffu, rec.y, j),
-                             __shfl_sync(0xffffffffu, rec.z, j), __shfl_sync(0xffffffffu, rec.w, j));
-    const int32_t row = m.x, base = m.y, len = m.w;
-    const int64_t k0 = (int64_t)(uint32_t)m.z;
-    const int w = len + 1;
-    int q = lane / w, c = lane - q * w;  // position of this lane, advanced by 32 values per step
-    const int step_q = 32 / w, step_c = 32 - step_q * w;
-    if (w <= 32 && !r.accumulate) {
-      // Rows of at most 31 columns: lane = column (lane len = RHS entry), so each store
-      // instruction writes one contiguous row segment of one equation; eight equations'
-      // values are read from shared memory before their eight stores are issued.
-      if (lane < w) {
-        const float* src = win + (base + (lane < len ? lane : r.maxcol)) * r.neqs;
-        float* dv = A_.values + (int64_t)A_.eq0 * A_.nnz + k0 + lane;
-        float* dr = A_.rhs + (int64_t)A_.eq0 * A_.n_node + row;
-        for (int q0 = 0; q0 < n_eq; q0 += 8) {
-          float v[8];
+  float* const values = A_.values + (int64_t)A_.eq0 * A_.nnz;
+  float* const rhs = A_.rhs + (int64_t)A_.eq0 * A_.n_node;
+  for (int f = 0; f < nf; f += 32) {
+    const int nr = min(32, nf - f);
+    int4 rec = make_int4(-2, 0, 0, 0);
+    if (lane < nr) rec = __ldg(r.flush_meta + f0 + f + lane);
+    const int row = rec.x, base = rec.y, len = rec.w;
+    const uint32_t k0 = (uint32_t)rec.z;  // first CSR position of the row (nnz < 2^31)
+    if (!r.accumulate) {
+      const int prev = __shfl_up_sync(0xffffffffu, row, 1);
+      unsigned starts = __ballot_sync(0xffffffffu, lane < nr && (lane == 0 || row != prev + 1));
+      while (starts) {
+        const int i0 = __ffs(starts) - 1;
+        starts &= starts - 1;
+        const int i1 = starts ? __ffs(starts) - 1 : nr;  // the run: records i0 .. i1 - 1
+        const uint32_t rk0 = __shfl_sync(0xffffffffu, k0, i0);
+        const uint32_t rend = __shfl_sync(0xffffffffu, k0 + (uint32_t)len, i1 - 1);
+        const int row0 = __shfl_sync(0xffffffffu, row, i0);
+        for (uint32_t c0 = rk0 & ~31u; c0 < rend; c0 += 32) {
+          const uint32_t pos = c0 + (uint32_t)lane;
+          const bool act = pos >= rk0 && pos < rend;
+          int ri = i0;  // the last record of the run whose first position is <= pos
 #pragma unroll
-          for (int k = 0; k < 8; ++k) v[k] = q0 + k < n_eq ? src[q0 + k] : 0.f;
+          for (int st = 16; st >= 1; st >>= 1) {
+            const int cand = ri + st;
+            const uint32_t kc = __shfl_sync(0xffffffffu, k0, cand < 32 ? cand : 31);
+            if (cand < i1 && kc <= pos) ri = cand;
+          }
+          const int rb = __shfl_sync(0xffffffffu, base, ri);
+          const uint32_t rk = __shfl_sync(0xffffffffu, k0, ri);
+          if (act) {
+            const float* src = win + (rb + (int)(pos - rk)) * r.neqs;
+            float* dst = values + pos;
+            for (int q0 = 0; q0 < n_eq; q0 += 8) {
+              float v[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            if (q0 + k >= n_eq) break;
-            if (lane < len) dv[(int64_t)(q0 + k) * A_.nnz] = v[k];
-            else dr[(int64_t)(q0 + k) * A_.n_node] = v[k];
+              for (int k = 0; k < 8; ++k) v[k] = q0 + k < n_eq ? src[q0 + k] : 0.f;
+#pragma unroll
+              for (int k = 0; k < 8; ++k)
+                if (q0 + k < n_eq) dst[(int64_t)(q0 + k) * A_.nnz] = v[k];
+            }
           }
         }
-      }
-    } else if (!r.accumulate) {
-#pragma unroll 4
-      for (int idx = lane; idx < w * n_eq; idx += 32) {
-        const float v = win[(base + (c < len ? c : r.maxcol)) * r.neqs + q];
-        float* dst = c < len ? A_.values + (int64_t)(A_.eq0 + q) * A_.nnz + k0 + c
-                             : A_.rhs + (int64_t)(A_.eq0 + q) * A_.n_node + row;
-        *dst = v;  // plain store: the L2 keeps the line until its neighbour row completes it
-        q += step_q;
-        c += step_c;
-        if (c >= w) {
-          c -= w;
-          ++q;
+        // the run's RHS entries: rows row0 .. row0 + (i1 - i0) - 1, lane l takes record i0 + l
+        const int rbl = __shfl_sync(0xffffffffu, base, min(i0 + lane, 31));
+        if (lane < i1 - i0) {
+          const float* src = win + (rbl + r.maxcol) * r.neqs;
+          float* dst = rhs + row0 + lane;
+          for (int q = 0; q < n_eq; ++q) dst[(int64_t)q * A_.n_node] = src[q];
         }
+        __syncwarp();
       }
     } else {
-      for (int idx = lane; idx < w * n_eq; idx += 32) {
-        const float v = win[(base + (c < len ? c : r.maxcol)) * r.neqs + q];
-        float* dst = c < len ? A_.values + (int64_t)(A_.eq0 + q) * A_.nnz + k0 + c
-                             : A_.rhs + (int64_t)(A_.eq0 + q) * A_.n_node + row;
-        *dst += v;
-        q += step_q;
-        c += step_c;
-        if (c >= w) {
-          c -= w;
-          ++q;
+      for (int i = 0; i < nr; ++i) {
+        const int rrow = __shfl_sync(0xffffffffu, row, i), rb = __shfl_sync(0xffffffffu, base, i);
+        const int rlen = __shfl_sync(0xffffffffu, len, i);
+        const uint32_t rk = __shfl_sync(0xffffffffu, k0, i);
+        const int w = rlen + 1;
+        for (int idx = lane; idx < w * n_eq; idx += 32) {
+          const int q = idx / w, c = idx - q * w;
+          const float v = win[(rb + (c < rlen ? c : r.maxcol)) * r.neqs + q];
+          float* dst = c < rlen ? values + (int64_t)q * A_.nnz + rk + c : rhs + (int64_t)q * A_.n_node + rrow;
+          *dst += v;
         }
       }
     }
     __syncwarp();
-    // clear the slot (contiguous, 16-byte aligned: row_stride is a multiple of 4)
-    float4* z = reinterpret_cast<float4*>(win + base * r.neqs);
-    for (int i = lane; i < r.row_stride * r.neqs / 4; i += 32) z[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    // clear the slots (contiguous, 16-byte aligned: row_stride is a multiple of 4)
+    for (int i = 0; i < nr; ++i) {
+      const int rb = __shfl_sync(0xffffffffu, base, i);
+      float4* z = reinterpret_cast<float4*>(win + rb * r.neqs);
+      for (int k = lane; k < r.row_stride * r.neqs / 4; k += 32) z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
   }
 }
 
