@@ -303,3 +303,44 @@ def update_fields(coords, phi, params):
     if st:
         raise ValueError(f"oracle update error {st}")
     return out
+
+
+class _Coefficients:
+    """Nodal arrays of one call (the attributes the element routines read)."""
+
+    def __init__(self, velocity, diffusivity, reaction, phi_old, dt):
+        self.velocity, self.diffusivity, self.reaction, self.phi_old, self.dt = (
+            velocity, diffusivity, reaction, phi_old, dt)
+
+
+def lumped_mass(elem_type, coords, conn):
+    """Row sums of the consistent mass matrix, M_L[i] = sum_j M_ij = int N_i dV (the lumped mass of
+    the explicit stepping of Sec. 2), as the mass operator applied to the vector of ones."""
+    n = coords.shape[0]
+    z = np.zeros((1, n))
+    c = _Coefficients(np.zeros((3, n)), z, z, z, 1.0)
+    return apply(elem_type, coords, conn, c, 0, np.ones(n), terms=MASS)
+
+
+def explicit_step(elem_type, coords, conn, fields, phi, dt, stages=3, terms=CONV | DIFF | REAC):
+    """One explicit time step of M_L dphi/dt = -A phi for every equation (Sec. 2: heat and species
+    advance by RK3 without an algebraic solver), A the operator of the chosen terms (convection,
+    diffusion, reaction; SUPG and the mass are not among them) applied matrix-free, M_L the lumped
+    mass.  stages = 1: forward Euler; stages = 3: the three-stage strong-stability-preserving
+    Runge-Kutta scheme
+        phi1 = phi + dt L(phi),  phi2 = 3/4 phi + 1/4 (phi1 + dt L(phi1)),
+        phi_new = 1/3 phi + 2/3 (phi2 + dt L(phi2)),   L(x) = -M_L^-1 A x.
+    phi is (n_eq, N); returns the new (n_eq, N) field in FP64."""
+    phi = np.asarray(phi, dtype=np.float64)
+    ml = lumped_mass(elem_type, coords, conn)
+
+    def L(x):
+        return np.stack([-apply(elem_type, coords, conn, fields, q, x[q], terms) for q in range(x.shape[0])]) / ml
+
+    if stages == 1:
+        return phi + dt * L(phi)
+    if stages != 3:
+        raise ValueError("stages must be 1 or 3")
+    p1 = phi + dt * L(phi)
+    p2 = 0.75 * phi + 0.25 * (p1 + dt * L(p1))
+    return phi / 3.0 + 2.0 / 3.0 * (p2 + dt * L(p2))

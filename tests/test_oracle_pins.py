@@ -975,6 +975,49 @@ def test_abs_rhs_summed_by_hand():
     check_abs_rhs_by_hand()
 
 
+# ------------------------------------------------------------------ explicit time stepping
+
+def check_explicit_step(t):
+    """The explicit step against closed forms (Sec. 2: RK3 without a solver; lumped mass):
+    - the lumped mass sums to the volume of the unit cube;
+    - a constant field with u, k arbitrary and s = 0 stays constant (C 1 = K 1 = 0);
+    - pure reaction s0 on a constant field c: the lumped system is dphi/dt = -s0 phi at every node,
+      so one step gives c (1 - z) (Euler) or c (1 - z + z^2/2 - z^3/6) (RK3), z = s0 dt;
+    - a linear field g.x + c under constant u, with k = s = 0: the Galerkin convection of a
+      linear field is (u.g) int N_i, so every node moves by -dt u.g exactly, for both schemes."""
+    n, frac = INV_MESH[t]
+    mesh = small_mesh(t, n, frac, seed=41)
+    N = mesh.n_node
+    ml = O.lumped_mass(t, mesh.coords, mesh.conn)
+    assert abs(ml.sum() - 1.0) < 1e-13 and np.all(ml > 0)
+    rng = np.random.default_rng(43)
+    u = G.velocity_field(mesh.coords)
+    zero = np.zeros((1, N))
+    f = G.Fields(u, rng.uniform(0.01, 0.1, (1, N)), zero, zero, 1e-3)
+    const = np.full((1, N), 0.7)
+    for st in (1, 3):
+        out = O.explicit_step(t, mesh.coords, mesh.conn, f, const, 2e-3, st)
+        assert np.abs(out - 0.7).max() < 1e-13
+    s0, dt, c = 3.0, 0.05, 1.3
+    fr = G.Fields(np.zeros((3, N)), zero, np.full((1, N), s0), zero, 1.0)
+    z = s0 * dt
+    e1 = O.explicit_step(t, mesh.coords, mesh.conn, fr, np.full((1, N), c), dt, 1)
+    e3 = O.explicit_step(t, mesh.coords, mesh.conn, fr, np.full((1, N), c), dt, 3)
+    assert np.abs(e1 - c * (1 - z)).max() < 1e-13
+    assert np.abs(e3 - c * (1 - z + z * z / 2 - z ** 3 / 6)).max() < 1e-13
+    g, u0 = np.array([0.4, -0.3, 0.9]), np.array([0.5, 0.2, -0.1])
+    lin = (mesh.coords @ g + 0.25)[None, :]
+    fc = G.Fields(np.tile(u0[:, None], (1, N)), zero, zero, zero, 1.0)
+    for st in (1, 3):
+        out = O.explicit_step(t, mesh.coords, mesh.conn, fc, lin, 0.01, st)
+        assert np.abs(out - (lin - 0.01 * u0 @ g)).max() < 1e-13
+
+
+@pytest.mark.parametrize("t", TYPES)
+def test_explicit_step_closed_forms(t):
+    check_explicit_step(t)
+
+
 def all_pins():
     rng = np.random.default_rng(1)
     pins = []
@@ -987,7 +1030,8 @@ def all_pins():
              lambda: check_bruteforce(O.HEX8), check_mixed, check_prism_closed_forms,
              *[lambda t=t: check_affine_high_order(t) for t in TYPES],
              *[lambda t=t: check_row_sampler(t) for t in TYPES], check_row_sampler_mixed,
-             *[lambda t=t: check_abs_sums(t) for t in TYPES], check_abs_rhs_by_hand]
+             *[lambda t=t: check_abs_sums(t) for t in TYPES], check_abs_rhs_by_hand,
+             *[lambda t=t: check_explicit_step(t) for t in TYPES]]
     try:
         import sympy  # noqa: F401  (the pyramid's exact integrals)
         pins.append(check_pyramid_closed_forms)
