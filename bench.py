@@ -365,6 +365,9 @@ def main():
                     help="also time the batched SpMV y_q = A_q x_q (fea_spmv) on the assembled matrices")
     ap.add_argument("--pcg", action="store_true",
                     help="also time the batched Jacobi-preconditioned CG (fea_pcg) on the MASS + DIFF matrices")
+    ap.add_argument("--explicit", action="store_true",
+                    help="also time explicit SSP-RK3 steps (fea_explicit_step: three matrix-free operator "
+                         "applications with the lumped mass) on the same workload")
     ap.add_argument("--laplacian", action="store_true",
                     help="also time the Laplacian of the same mesh (the DIFF term alone, k = 1, one equation)")
     ap.add_argument("--graph", type=int, default=None,
@@ -581,6 +584,21 @@ def main():
             out["laplacian"]["parity"] = sampled_parity(G.Workload(w.name, m, lf, w.precision), lv, lr, p, nnz,
                                                         terms=fea.FEA_TERM_DIFF)
         del ld, lv, lr
+    if args.explicit:
+        phx = dev[3].clone()
+        xo = fea.fea_default_opts()
+        fea.fea_explicit_step(h, p, *dev[:3], phx, 1e-4, q, 3, xo)  # lumped mass and workspace
+        xa, xb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        xa.record(stream)
+        for _ in range(3):
+            fea.fea_explicit_step(h, p, *dev[:3], phx, 1e-4, q, 3, xo)
+        xb.record(stream)
+        torch.cuda.synchronize()
+        xms = xa.elapsed_time(xb) / 3
+        out["explicit_rk3"] = {"ms_per_step": xms, "value": m.n_elem * q / (xms * 1e-3), "unit": UNIT,
+                               "what": "one SSP-RK3 step of M_L dphi/dt = -(C + K + R) phi, FP32: three "
+                                       "matrix-free operator applications and stage updates"}
+        del phx
     if args.residual:
         r = torch.empty((q, m.n_node), dtype=torch.float32, device="cuda")
         ro = fea.fea_default_opts()

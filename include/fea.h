@@ -265,6 +265,29 @@ FEA_API fea_status fea_residual(fea_mesh* mesh, const fea_pattern* pattern, cons
                                 double dt, int32_t n_eq, const fea_assemble_opts* opts, void* r);
 
 /*
+ * fea_explicit_step -- one explicit time step of every equation (Sec. 2: heat and species
+ * advance by a third-order Runge-Kutta scheme without an algebraic solver):
+ *     M_L dphi/dt = -A phi,
+ * A the convection, diffusion and reaction terms of the operator (those selected by opts->terms
+ * among FEA_TERM_CONV, FEA_TERM_DIFF, FEA_TERM_REAC; the mass and SUPG bits are ignored), applied
+ * element by element as in fea_residual, and M_L[i] = sum_j M_ij = int N_i dV the row-sum lumped
+ * mass.  stages = 1: forward Euler phi += dt L(phi); stages = 3: the strong-stability-preserving
+ * RK3 scheme phi1 = phi + dt L(phi), phi2 = 3/4 phi + 1/4 (phi1 + dt L(phi1)),
+ * phi = 1/3 phi + 2/3 (phi2 + dt L(phi2)), with L(x) = -M_L^-1 A x.
+ *   velocity, diffusivity, reaction: as in fea_assemble (DEVICE arrays of the precision in opts)
+ *   phi  [n_eq][n_node] DEVICE array: the field, advanced in place
+ *   dt   > 0; keeping it within the explicit stability limit is the caller's part
+ * The lumped mass is computed by the first call for a pattern and precision (it waits for the
+ * stream once) and kept; the stage buffers (3 n_eq n_node values) are a device workspace owned
+ * by the pattern, grown on demand.  Enqueued on the mesh's stream; opts->event_begin/event_end
+ * bracket the step.  FEA_ERR_ARG for stages other than 1 or 3, or a term mask with none of the
+ * three terms.
+ */
+FEA_API fea_status fea_explicit_step(fea_mesh* mesh, const fea_pattern* pattern, const void* velocity,
+                                     const void* diffusivity, const void* reaction, void* phi, double dt,
+                                     int32_t n_eq, int32_t stages, const fea_assemble_opts* opts);
+
+/*
  * fea_assemble_host -- the same operation on HOST arrays (same shapes and
  * types as fea_assemble).  Copies the inputs to a device workspace owned by the
  * pattern, assembles, copies values and rhs back, and waits for completion.

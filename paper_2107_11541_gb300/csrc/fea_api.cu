@@ -1033,6 +1033,9 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->em);
   cudaFree(p->diag);
   cudaFree(p->pcg_ws);
+  cudaFree(p->lumped[0]);
+  cudaFree(p->lumped[1]);
+  cudaFree(p->rk_ws);
   cudaFree(p->elem_order);
   cudaFree(p->hex8_fnode);
   for (auto& kv : p->cancel) {

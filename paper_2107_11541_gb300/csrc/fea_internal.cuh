@@ -121,6 +121,10 @@ struct fea_pattern {
   int32_t* diag;
   void* pcg_ws;
   size_t pcg_bytes;
+  // fea_explicit_step: lumped mass per precision ([0] FP32, [1] FP64, [N]) and the stage workspace
+  void* lumped[2];
+  void* rk_ws;
+  size_t rk_bytes;
   // node-major fields for the batched Hex8 kernel on the Hex8 block of a mixed mesh
   float* hex8_fnode;
   size_t hex8_fnode_bytes;

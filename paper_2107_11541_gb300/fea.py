@@ -28,6 +28,7 @@ NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27, FEA_PEN6: 6, FEA_PYR5: 5}
 # Every symbol include/fea.h declares (checked by the tests).
 EXPORTS = ["fea_default_opts", "fea_mesh_create", "fea_mesh_create_mixed", "fea_mesh_destroy", "fea_mesh_set_stream", "fea_sync",
            "fea_pattern_build", "fea_pattern_get", "fea_pattern_destroy", "fea_assemble", "fea_residual",
+           "fea_explicit_step",
            "fea_assemble_host",
            "fea_pack_plan", "fea_csr_rowptr_noalloc", "fea_update_fields", "fea_graph_capture_steps",
            "fea_graph_launch", "fea_graph_destroy", "fea_spmv", "fea_pcg", "fea_tuned_strategy", "fea_tuned_config",
@@ -83,6 +84,7 @@ def lib(path: str = LIB_PATH):
         L.fea_assemble.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(fea_assemble_opts), vp, vp]
         L.fea_assemble_host.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(fea_assemble_opts), vp, vp]
         L.fea_residual.argtypes = [vp, vp, vp, vp, vp, vp, vp, dbl, i32, C.POINTER(fea_assemble_opts), vp]
+        L.fea_explicit_step.argtypes = [vp, vp, vp, vp, vp, vp, dbl, i32, i32, C.POINTER(fea_assemble_opts)]
         L.fea_pack_plan.argtypes = [vp, i32, i32, vp, vp]
         L.fea_csr_rowptr_noalloc.argtypes = [vp, i64, vp, vp]
         L.fea_update_fields.argtypes = [vp, vp, i32, vp]
@@ -206,6 +208,14 @@ def fea_residual(mesh, pattern, velocity, diffusivity, reaction, phi_old, phi, d
     """Matrix-free residual r = b - A phi (torch CUDA tensors of the precision's dtype)."""
     _check(lib().fea_residual(mesh, pattern, _ptr(velocity), _ptr(diffusivity), _ptr(reaction), _ptr(phi_old),
                               _ptr(phi), float(dt), int(n_eq), C.byref(opts) if opts is not None else None, _ptr(r)))
+
+
+def fea_explicit_step(mesh, pattern, velocity, diffusivity, reaction, phi, dt: float, n_eq: int, stages: int = 3,
+                      opts=None):
+    """One explicit step (forward Euler or SSP-RK3) of M_L dphi/dt = -A phi, phi advanced in place
+    (device tensors of the precision in opts)."""
+    _check(lib().fea_explicit_step(mesh, pattern, _ptr(velocity), _ptr(diffusivity), _ptr(reaction), _ptr(phi),
+                                   float(dt), int(n_eq), int(stages), C.byref(opts) if opts is not None else None))
 
 
 def fea_assemble_host(mesh, pattern, velocity, diffusivity, reaction, phi_old, dt: float, n_eq: int, opts, values,
