@@ -147,9 +147,10 @@ typedef struct {
   int32_t cancel_check;     /* FP32 path: 1 = rows whose sums cancel are redone in FP64 (see
                                fea_cancel_rows); not allowed with accumulate.  Default 0 */
   int32_t host_parts;       /* fea_assemble_host only: the equations are assembled in this many parts,
-                               each part's values copied back while the next part computes (at most
-                               n_eq); 0 = automatic: 3 when the values exceed 256 MB and n_eq >= 3,
-                               else 1.  Default 0 */
+                               each part's inputs copied in and values copied back while other parts
+                               compute (at most n_eq); 0 = automatic: when the values exceed 256 MB and
+                               n_eq >= 3, about 8 GB of values per part and at least 3 parts, else 1.
+                               Default 0 */
   int32_t contraction;      /* fea_contraction: how the FP32 Hex27 element matrices (full operator, up to
                                12 equations) are contracted; other element types and the residual use
                                the CUDA cores.  Default FEA_CONTRACT_AUTO */
@@ -290,7 +291,9 @@ FEA_API fea_status fea_explicit_step(fea_mesh* mesh, const fea_pattern* pattern,
 /*
  * fea_assemble_host -- the same operation on HOST arrays (same shapes and
  * types as fea_assemble).  Copies the inputs to a device workspace owned by the
- * pattern, assembles, copies values and rhs back, and waits for completion.
+ * pattern, assembles, copies values and rhs back, and waits for completion.  With
+ * several parts (opts->host_parts) each part's field slices are copied in on their own
+ * streams ahead of its assembly and its values copied back while later parts compute.
  * Pinned host memory gives the fastest copies.
  */
 FEA_API fea_status fea_assemble_host(fea_mesh* mesh, const fea_pattern* pattern, const void* velocity,

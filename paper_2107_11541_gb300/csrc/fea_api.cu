@@ -885,6 +885,8 @@ fea_status fea_mesh_destroy(fea_mesh* m) {
   if (m->copy_ready) {
     for (int i = 0; i < fea_mesh::N_COPY; ++i) cudaStreamDestroy(m->copy_stream[i]);
     for (int i = 0; i <= fea_mesh::N_COPY; ++i) cudaEventDestroy(m->copy_event[i]);
+    for (int i = 0; i < fea_mesh::N_IN; ++i) cudaStreamDestroy(m->in_stream[i]);
+    for (cudaEvent_t e : m->part_events) cudaEventDestroy(e);
   }
   delete m;
   return FEA_OK;
@@ -1289,6 +1291,8 @@ fea_status fea_assemble_host(fea_mesh* m, const fea_pattern* cp, const void* vel
   if (!m->copy_ready) {
     for (int i = 0; i < NC; ++i) FEA_CUDA_TRY(cudaStreamCreateWithFlags(&m->copy_stream[i], cudaStreamNonBlocking));
     for (int i = 0; i <= NC; ++i) FEA_CUDA_TRY(cudaEventCreateWithFlags(&m->copy_event[i], cudaEventDisableTiming));
+    for (int i = 0; i < fea_mesh::N_IN; ++i)
+      FEA_CUDA_TRY(cudaStreamCreateWithFlags(&m->in_stream[i], cudaStreamNonBlocking));
     m->copy_ready = true;
   }
   cudaEvent_t start = m->copy_event[NC];  // recorded on s before each batch of copies
@@ -1316,25 +1320,57 @@ fea_status fea_assemble_host(fea_mesh* m, const fea_pattern* cp, const void* vel
       out[n++] = to_dev ? Copy{d + off, h + off, b} : Copy{(void*)(h + off), d + off, b};
     }
   };
-  Copy in[4 + 2 * NC];
-  int n_in = 0;
-  in[n_in++] = Copy{d_vel, vel, b_vel};
-  in[n_in++] = Copy{d_kd, kd, b_f};
-  in[n_in++] = Copy{d_sr, sr, b_f};
-  in[n_in++] = Copy{d_phi, phi, b_f};
-  if (o.accumulate) {
+  // Large outputs: the equations are assembled in parts, each an independent assembly of its
+  // slices, so that part k's values travel back while part k+1 computes; about 8 GB of values
+  // per part (3 parts at least: 3 measured best of 3 and 6 on 5 GB of values).
+  const int parts = o.host_parts > 0 ? std::min(o.host_parts, n_eq)
+                    : (b_val > ((size_t)256 << 20) && n_eq >= 3)
+                        ? std::min<int>(n_eq, std::max<int>(3, (int)((b_val + (8ull << 30) - 1) / (8ull << 30))))
+                        : 1;
+  const int per = (n_eq + parts - 1) / parts;
+  if (o.accumulate) {  // the outputs travel in as well: every input first, then the parts
+    Copy in[4 + 2 * NC];
+    int n_in = 0;
+    in[n_in++] = Copy{d_vel, vel, b_vel};
+    in[n_in++] = Copy{d_kd, kd, b_f};
+    in[n_in++] = Copy{d_sr, sr, b_f};
+    in[n_in++] = Copy{d_phi, phi, b_f};
     split(in, n_in, d_val, (const char*)values, b_val, true);
     in[n_in++] = Copy{d_rhs, rhs, b_f};
+    FEA_TRY(run_copies(in, n_in, cudaMemcpyHostToDevice, true));
+  } else {
+    // each part's inputs on the host-to-device streams, so that part k's assembly waits only for
+    // its own slices (the velocity goes first); the copies start after the work already on s
+    constexpr int NI = fea_mesh::N_IN;
+    while ((int)m->part_events.size() < NI * parts) {
+      cudaEvent_t e;
+      FEA_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      m->part_events.push_back(e);
+    }
+    FEA_CUDA_TRY(cudaEventRecord(start, s));
+    for (int i = 0; i < NI; ++i) FEA_CUDA_TRY(cudaStreamWaitEvent(m->in_stream[i], start, 0));
+    FEA_CUDA_TRY(cudaMemcpyAsync(d_vel, vel, b_vel, cudaMemcpyHostToDevice, m->in_stream[0]));
+    for (int k = 0, q0 = 0; q0 < n_eq; ++k, q0 += per) {
+      const int cnt = std::min(per, n_eq - q0);
+      const size_t fo = es * (size_t)q0 * N, fb = es * (size_t)cnt * N;
+      const char* src[3] = {(const char*)kd, (const char*)sr, (const char*)phi};
+      char* dst[3] = {d_kd, d_sr, d_phi};
+      for (int f = 0; f < 3; ++f) {  // each slice in NI pieces, cut at 256-byte boundaries
+        const size_t piece = ((fb + NI - 1) / NI + 255) & ~(size_t)255;
+        for (size_t off = 0, i = 0; off < fb; off += piece, ++i) {
+          const size_t b = std::min(piece, fb - off);
+          FEA_CUDA_TRY(cudaMemcpyAsync(dst[f] + fo + off, src[f] + fo + off, b, cudaMemcpyHostToDevice,
+                                       m->in_stream[i % NI]));
+        }
+      }
+      for (int i = 0; i < NI; ++i) FEA_CUDA_TRY(cudaEventRecord(m->part_events[NI * k + i], m->in_stream[i]));
+    }
   }
-  FEA_TRY(run_copies(in, n_in, cudaMemcpyHostToDevice, true));
-  // Large outputs: the equations are assembled in parts, each an independent assembly of its
-  // slices, so that part k's values travel back while part k+1 computes.
-  const int parts = o.host_parts > 0 ? std::min(o.host_parts, n_eq)
-                                      : (b_val > ((size_t)256 << 20) && n_eq >= 3) ? 3 : 1;  // 3: best of 3 and 6
-  const int per = (n_eq + parts - 1) / parts;
-  for (int q0 = 0; q0 < n_eq; q0 += per) {
+  for (int k = 0, q0 = 0; q0 < n_eq; ++k, q0 += per) {
     const int cnt = std::min(per, n_eq - q0);
     const size_t fo = es * (size_t)q0 * N, vo = es * (size_t)q0 * nnz;
+    if (!o.accumulate)
+      for (int i = 0; i < fea_mesh::N_IN; ++i) FEA_CUDA_TRY(cudaStreamWaitEvent(s, m->part_events[fea_mesh::N_IN * k + i], 0));
     FEA_TRY(fea_assemble(m, p, d_vel, d_kd + fo, d_sr + fo, d_phi + fo, dt, cnt, &o, d_val + vo, d_rhs + fo));
     Copy outc[2 * NC + 1];
     int n_out = 0;

@@ -78,10 +78,14 @@ struct fea_mesh {
   std::vector<Block> blocks;
   bool mixed;            // more than one block
   int32_t* conn_blocks;  // several types: the blocks' own connectivity, concatenated
-  // fea_assemble_host: side streams and events for concurrent host<->device copies
+  // fea_assemble_host: side streams and events for concurrent host<->device copies (N_COPY
+  // device-to-host streams, N_IN host-to-device streams, and per-part events grown on demand)
   static constexpr int N_COPY = 4;
+  static constexpr int N_IN = 2;
   cudaStream_t copy_stream[N_COPY];
   cudaEvent_t copy_event[N_COPY + 1];
+  cudaStream_t in_stream[N_IN];
+  std::vector<cudaEvent_t> part_events;
   bool copy_ready;
 };
 
