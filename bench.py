@@ -351,6 +351,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + sorted(MIXED_WORKLOADS))
     ap.add_argument("--scatter", type=int, default=0, help="0 auto, 1 atomic, 2 row-owned, 3 gather")
+    ap.add_argument("--mapping", type=int, default=0,
+                    help="Gauss-point mapping: 0 auto, 1 type kernel, 2 warp per element, 3 two threads per item "
+                         "(row-owned Hex8)")
+    ap.add_argument("--eq-groups", type=int, default=0, help="row-owned equation groups (0: tuned or 1)")
+    ap.add_argument("--host-parts", type=int, default=0, help="parts of the end-to-end call (0: automatic)")
     ap.add_argument("--contraction", type=int, default=0,
                     help="Hex27 element matrices: 0 auto, 1 CUDA cores, 2 tensor cores bf16x3, 3 tensor cores bf16x6")
     ap.add_argument("--no-e2e", action="store_true")
@@ -420,7 +425,8 @@ def main():
         values = torch.empty((q, nnz), dtype=torch.float32, device="cuda")
         rhs = torch.empty((q, m.n_node), dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
-    opts = fea.fea_default_opts(scatter=args.scatter, contraction=args.contraction)
+    opts = fea.fea_default_opts(scatter=args.scatter, contraction=args.contraction, mapping=args.mapping,
+                                eq_groups=args.eq_groups)
 
     def step(ev=None):
         if ev is not None:
@@ -638,7 +644,8 @@ def main():
 
     if not args.no_e2e:
         out["e2e"] = end_to_end(h, p, f32, m, nnz, q, stream, min(args.steps, 5), world, dist, values_dev=values,
-                                parity_of=(w0, None) if rank == 0 and not args.no_parity else None)
+                                parity_of=(w0, None) if rank == 0 and not args.no_parity else None,
+                                host_parts=args.host_parts)
 
     if rank == 0 and world == 1 and not args.no_cpu:
         w = w0
@@ -945,7 +952,7 @@ def host_memory_available() -> int:
     return avail if avail is not None else 0
 
 
-def end_to_end(h, p, f32, m, nnz, q, stream, steps, world, dist, values_dev=None, parity_of=None):
+def end_to_end(h, p, f32, m, nnz, q, stream, steps, world, dist, values_dev=None, parity_of=None, host_parts=0):
     """Same metric through fea_assemble_host: pinned host inputs copied in, values and RHS read back.
     Also the copy floor of this box: one cudaMemcpyAsync per direction of the step's bytes between
     pinned host memory and the device (values_dev, the device-resident values of the same size, is
@@ -962,7 +969,7 @@ def end_to_end(h, p, f32, m, nnz, q, stream, steps, world, dist, values_dev=None
            for a in (f32.velocity, f32.diffusivity, f32.reaction, f32.phi_old)]
     hv = torch.empty((q, nnz), dtype=torch.float32).pin_memory()
     hr = torch.empty((q, m.n_node), dtype=torch.float32).pin_memory()
-    opts = fea.fea_default_opts()
+    opts = fea.fea_default_opts(host_parts=host_parts)
     fea.fea_assemble_host(h, p, *pin, f32.dt, q, opts, hv, hr)
     times = []
     for _ in range(steps):

@@ -127,8 +127,11 @@ typedef enum {
                                    equation) walking the Gauss points (Tet4, Pen6, Pyr5; batched for Hex8,
                                    with one thread per (element, Gauss point) for the shared geometry), or one
                                    CTA per element with threads over (Gauss point, node) tasks (Hex27) */
-  FEA_MAP_WARP_PER_ELEMENT = 2  /* one warp per element, any type: lanes over the Gauss points for the
+  FEA_MAP_WARP_PER_ELEMENT = 2, /* one warp per element, any type: lanes over the Gauss points for the
                                    geometry, then over the matrix entries */
+  FEA_MAP_TWO_THREADS_PER_ITEM = 3 /* row-owned Hex8 scatter, full operator: two threads per (element,
+                                   equation), each forming four rows of the element matrix, in CTAs of 512
+                                   threads (twice the warps per SM); elsewhere as FEA_MAP_TYPE_KERNEL */
 } fea_mapping;
 
 typedef struct {

@@ -382,7 +382,7 @@ static fea_status check_assemble_args(fea_mesh* m, const fea_pattern* p, const v
   if (o->host_parts < 0) return fail(FEA_ERR_ARG, "host_parts must be >= 0");
   if (o->contraction < FEA_CONTRACT_AUTO || o->contraction > FEA_CONTRACT_TC_TF32X3)
     return fail(FEA_ERR_ARG, "unknown contraction");
-  if (o->mapping < FEA_MAP_AUTO || o->mapping > FEA_MAP_WARP_PER_ELEMENT) return fail(FEA_ERR_ARG, "unknown mapping");
+  if (o->mapping < FEA_MAP_AUTO || o->mapping > FEA_MAP_TWO_THREADS_PER_ITEM) return fail(FEA_ERR_ARG, "unknown mapping");
   if (o->elems_per_cta < 0 || o->elems_per_cta > 256) return fail(FEA_ERR_ARG, "elems_per_cta must be in [0, 256]");
   if (m->mixed && (o->scatter == FEA_SCATTER_ROWOWNED || o->scatter == FEA_SCATTER_GATHER || o->cancel_check))
     return fail(FEA_ERR_ARG, "a mesh of several element types scatters with atomics (no row-owned, gather or "
@@ -598,8 +598,11 @@ std::vector<Strategy> candidates(fea_mesh* m, fea_pattern* p, int32_t n_eq, int 
       const int size = plan_group_size(n_eq, g);
       if (size == last) continue;
       last = size;
-      c.push_back(Strategy{FEA_SCATTER_ROWOWNED, g, T, 0, CU});
-      for (int be : {16, 32}) c.push_back(Strategy{FEA_SCATTER_ROWOWNED, g, T, be, CU});
+      for (int mp : {T, (int)FEA_MAP_TWO_THREADS_PER_ITEM}) {
+        if (mp != T && terms != FEA_TERM_ALL) continue;  // the two-thread kernel forms the full operator
+        c.push_back(Strategy{FEA_SCATTER_ROWOWNED, g, mp, 0, CU});
+        for (int be : {16, 32}) c.push_back(Strategy{FEA_SCATTER_ROWOWNED, g, mp, be, CU});
+      }
     }
   }
   std::vector<int> batches{0};
@@ -781,11 +784,11 @@ fea_status choose_strategy(fea_mesh* m, fea_pattern* p, const void* vel, const v
     if (c.scatter == FEA_SCATTER_ROWOWNED && c.batch != 0) continue;
     if ((status = time_one(c)) != FEA_OK) break;
   }
-  // stage 2: the row-owned batch sizes, for the best group count only
+  // stage 2: the row-owned batch sizes, for the best group count and mapping only
   if (status == FEA_OK && best.scatter == FEA_SCATTER_ROWOWNED) {
-    const int g = best.groups;
+    const int g = best.groups, mp = best.mapping;
     for (const Strategy& c : all)
-      if (c.scatter == FEA_SCATTER_ROWOWNED && c.batch != 0 && c.groups == g)
+      if (c.scatter == FEA_SCATTER_ROWOWNED && c.batch != 0 && c.groups == g && c.mapping == mp)
         if ((status = time_one(c)) != FEA_OK) break;
   }
   cudaEventDestroy(e0);

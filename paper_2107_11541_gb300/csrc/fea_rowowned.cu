@@ -544,13 +544,15 @@ static fea_status assemble_group(ro::Variant* v, const AsmArgs<float>& a, int ac
   r.neqs = v->neqs;
   r.accumulate = accumulate;
   r.be = v->be;
-  auto kern = a.terms == FEA_TERM_ALL ? ro::k_rowowned_hex8<true> : ro::k_rowowned_hex8<false>;
+  const bool two = a.mapping == FEA_MAP_TWO_THREADS_PER_ITEM && a.terms == FEA_TERM_ALL;
+  auto kern = two ? ro::k_rowowned_hex8_half
+                  : a.terms == FEA_TERM_ALL ? ro::k_rowowned_hex8<true> : ro::k_rowowned_hex8<false>;
   FEA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem));
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   unsigned grid = (unsigned)std::max(1, std::min(v->n_units, nsm));
-  kern<<<grid, ro::THREADS, v->smem, s>>>(r);
+  kern<<<grid, two ? ro::THREADS_HALF : ro::THREADS, v->smem, s>>>(r);
   FEA_CUDA_TRY(cudaGetLastError());
   count_launches(1);
   return FEA_OK;

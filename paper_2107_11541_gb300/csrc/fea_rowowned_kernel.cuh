@@ -76,22 +76,24 @@ struct Stage {
   float* raw;      // [be][8][RAW]
 };
 
-// Issues the copies of the plan data (node ids, offsets) of batch t into buffer s.
+// Issues the copies of the plan data (node ids, offsets) of batch t into buffer s (a CTA of NT threads).
+template <int NT = THREADS>
 __device__ __forceinline__ void stage_plan(const RoArgs& r, int t, const Stage& s) {
   const int v0 = r.batch_visit[t], nv = r.batch_visit[t + 1] - v0;
   const int32_t* vn = r.visit_nodes + (int64_t)v0 * NEN;
-  for (int i = threadIdx.x; i < nv * NEN; i += THREADS) cp_async4(s.nid + i, vn + i);
+  for (int i = threadIdx.x; i < nv * NEN; i += NT) cp_async4(s.nid + i, vn + i);
   const uint32_t* vo = reinterpret_cast<const uint32_t*>(r.visit_off + (int64_t)v0 * OFFS);
   uint32_t* so = reinterpret_cast<uint32_t*>(s.off);
-  for (int i = threadIdx.x; i < nv * OFFS / 2; i += THREADS) cp_async4(so + i, vo + i);
+  for (int i = threadIdx.x; i < nv * OFFS / 2; i += NT) cp_async4(so + i, vo + i);
 }
 
 // Issues the gathers of the raw node data of batch t (node ids already in buffer s).
+template <int NT = THREADS>
 __device__ __forceinline__ void stage_nodes(const RoArgs& r, int t, const Stage& s) {
   const AsmArgs<float>& A_ = r.a;
   const int nv = r.batch_visit[t + 1] - r.batch_visit[t];
   const int64_t N = A_.n_node;
-  for (int i = threadIdx.x; i < nv * NEN * RAW; i += THREADS) {
+  for (int i = threadIdx.x; i < nv * NEN * RAW; i += NT) {
     const int node = i / RAW, c = i - node * RAW;
     const int64_t n = s.nid[node];
     const float* src = c < 3   ? A_.xhi + (int64_t)c * N + n
@@ -504,6 +506,200 @@ __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
     // the rows the last batch completed, by all warps
     __syncthreads();
     flush_rows(r, win, t1 - 1, warp, THREADS / 32);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ two threads per item
+
+// The half-item sums of the full operator: rows a = 4H .. 4H + 3 of one (element, equation)
+// item's matrix and RHS.  The same Gauss-point sums as item_sums<true>, restricted to four
+// rows: Am[r][c] = sum_g P_(4H+r)(g) (Q_(2c), Q_(2c+1))(g), Dh[r][c] the diffusion entries of
+// those rows (the symmetric storage read for both (a, b) and (b, a)), bv2 the RHS of the rows.
+template <int H>
+__device__ __forceinline__ void half_sums(const float* Ge, float ck, const float kg[NG], const float sg[NG],
+                                          const float pg[NG], float inv_dt, float2 (&Am)[4][NEN / 2],
+                                          float2 (&Dh)[4][NEN / 2], float2 (&bv2)[2]) {
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    const float4* G4 = reinterpret_cast<const float4*>(Ge + g * GEO);
+    float gv[12];
+#pragma unroll
+    for (int k2 = 0; k2 < 3; ++k2) {
+      const float4 x = G4[k2];
+      gv[4 * k2] = x.x;
+      gv[4 * k2 + 1] = x.y;
+      gv[4 * k2 + 2] = x.z;
+      gv[4 * k2 + 3] = x.w;
+    }
+    const float dv = gv[0];
+    const float den = fmaf(ck, kg[g], gv[1] + sg[g]);
+    const float tau = den > 0.f ? __fdividef(1.f, den) : 0.f;
+    const float dvt = dv * tau;
+    const float sigs = inv_dt + sg[g];
+    float P[4], Q[NEN];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) P[a] = fmaf(dvt, gv[2 + 4 * H + a], dv * hex_n(4 * H + a, g));
+#pragma unroll
+    for (int b = 0; b < NEN; ++b) Q[b] = fmaf(sigs, hex_n(b, g), gv[2 + b]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float2 pa = make_float2(P[a], P[a]);
+#pragma unroll
+      for (int c = 0; c < NEN / 2; ++c) Am[a][c] = __ffma2_rn(pa, make_float2(Q[2 * c], Q[2 * c + 1]), Am[a][c]);
+    }
+    // diffusion: entry (a, b) of the symmetric D sits at gv[10 + sym_index(min, max)]; walk the
+    // stored entries in float4 pieces and add each to the rows of this half it belongs to
+    const float kk = kg[g];
+#pragma unroll
+    for (int c4 = 2; c4 < GEO / 4; ++c4) {
+      const float4 x = G4[c4];
+      const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = 4 * c4 + j - 10;  // symmetric index of this stored entry
+        if (e < 0 || e >= 36) continue;
+        int a = 0;
+        while (a < NEN - 1 && sym_index(a + 1, a + 1) <= e) ++a;  // row of e in the upper triangle
+        const int b = a + (e - sym_index(a, a));
+        if (a >= 4 * H && a < 4 * H + 4) {
+          float& dst = (b & 1) ? Dh[a - 4 * H][b / 2].y : Dh[a - 4 * H][b / 2].x;
+          dst = fmaf(kk, xv[j], dst);
+        }
+        if (b != a && b >= 4 * H && b < 4 * H + 4) {
+          float& dst = (a & 1) ? Dh[b - 4 * H][a / 2].y : Dh[b - 4 * H][a / 2].x;
+          dst = fmaf(kk, xv[j], dst);
+        }
+      }
+    }
+    const float pdt = pg[g] * inv_dt;
+    bv2[0] = __ffma2_rn(make_float2(P[0], P[1]), make_float2(pdt, pdt), bv2[0]);
+    bv2[1] = __ffma2_rn(make_float2(P[2], P[3]), make_float2(pdt, pdt), bv2[1]);
+  }
+}
+
+// The row-owned kernel with two threads per (element, equation) item, each forming four rows of
+// the element matrix (half H = 0: rows 0-3, H = 1: rows 4-7), in CTAs of THREADS_HALF threads:
+// half the accumulators per thread, so twice the warps per SM, at the price of the
+// interpolation and the Gauss-point scalars computed by both threads.  Items run as
+// [half][element][equation], each half padded to whole warps, so a warp's threads share H.
+// Same plan, batches, scatter rounds (round rho writes row 4 H + rho) and flush as
+// k_rowowned_hex8; full operator only.
+constexpr int THREADS_HALF = 512;
+
+__global__ void __launch_bounds__(THREADS_HALF, 1) k_rowowned_hex8_half(RoArgs r) {
+  constexpr int NT = THREADS_HALF;
+  extern __shared__ __align__(16) float sm_roh[];
+  const AsmArgs<float>& A_ = r.a;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int be = r.be;
+  const int win_floats = r.n_slots * r.row_stride * r.neqs;
+  float* win = sm_roh;
+  float* geo = win + ((win_floats + 3) & ~3);
+  float* const stage0 = geo + be * GEO_ELEM;
+  const int stage_floats = be * (NEN * RAW + NEN + OFFS / 2);
+  auto stage = [&](int b) {
+    float* p = stage0 + b * stage_floats;
+    Stage s;
+    s.raw = p;
+    s.nid = reinterpret_cast<int32_t*>(p + be * NEN * RAW);
+    s.off = reinterpret_cast<uint16_t*>(p + be * NEN * RAW + be * NEN);
+    return s;
+  };
+  const float inv_dt = (float)(1.0 / A_.dt);
+  const int n_eq = A_.eq_count;
+
+  for (int i = tid; i < win_floats; i += NT) win[i] = 0.f;
+
+  const int G = gridDim.x;
+  for (int k = 0;; ++k) {
+    const int u = (k & 1) ? (k + 1) * G - 1 - (int)blockIdx.x : k * G + (int)blockIdx.x;
+    if (u >= r.n_units) break;
+    const int t0 = r.unit_batch[2 * u], t1 = r.unit_batch[2 * u + 1];
+    stage_plan<NT>(r, t0, stage(0));
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    stage_nodes<NT>(r, t0, stage(0));
+    cp_async_commit();
+    if (t0 + 1 < t1) stage_plan<NT>(r, t0 + 1, stage(1));
+    cp_async_commit();
+    for (int t = t0; t < t1; ++t) {
+      const Stage S = stage((t - t0) & 1);
+      const Stage Sn = stage((t - t0 + 1) & 1);
+      const int nv = r.batch_visit[t + 1] - r.batch_visit[t];
+      const int items1 = nv * n_eq, hstride = (items1 + 31) & ~31;  // items of one half, padded
+      cp_async_wait_all();
+      __syncthreads();
+      if (t + 1 < t1) stage_nodes<NT>(r, t + 1, Sn);
+      cp_async_commit();
+      const int gw = (nv * NG + 31) / 32;
+      if (warp < gw) geometry(r, S, geo, tid >> 3, tid & 7, (tid >> 3) < nv);
+      __syncthreads();
+      const int rounds = max(1, (2 * hstride + NT - 1) / NT);
+      const int flush_at = rounds >= 2 ? 1 : 0;
+      for (int it = 0; it < rounds; ++it) {
+        if (it == flush_at && t > t0) flush_rows(r, win, t - 1, warp, NT / 32);
+        const int item = tid + it * NT;
+        const int H = item >= hstride ? 1 : 0;  // the same for the whole warp (hstride % 32 == 0)
+        const int li = item - H * hstride;
+        const bool has = H < 2 && item < 2 * hstride && li < items1;
+        const int el = has ? li / n_eq : 0, q = has ? li - el * n_eq : 0;
+        const uint32_t* eo = reinterpret_cast<const uint32_t*>(S.off + el * OFFS);
+        float2 Am[4][NEN / 2], Dh[4][NEN / 2], bv2[2];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < NEN / 2; ++c) Am[a][c] = Dh[a][c] = make_float2(0.f, 0.f);
+        bv2[0] = bv2[1] = make_float2(0.f, 0.f);
+        if (has) {
+          float kn[NEN], sn[NEN], pn[NEN];
+          load_fields(r, S, el, q, kn, sn, pn);
+          const float* Ge = geo + el * GEO_ELEM;
+          const float ck = Ge[NG * GEO];
+          float kg[NG], sg[NG], pg[NG];
+          interp8(kn, kg);
+          interp8(sn, sg);
+          interp8(pn, pg);
+          if (H == 0) half_sums<0>(Ge, ck, kg, sg, pg, inv_dt, Am, Dh, bv2);
+          else half_sums<1>(Ge, ck, kg, sg, pg, inv_dt, Am, Dh, bv2);
+        }
+        // round rho: this thread's row a = 4 H + rho (rows rho and rho + 4 of every element are
+        // written in round rho, as in the one-thread kernel)
+#pragma unroll
+        for (int rho = 0; rho < ROUNDS; ++rho) {
+          if (has) {
+            const int a = 4 * H + rho;
+            const uint32_t rw = eo[(NEN * NEN + a) / 2];
+            const uint32_t ro = (a & 1) ? (rw >> 16) : (rw & 0xFFFFu);
+            if (ro != NONE) {
+              float* p[NEN + 1];
+              float add[NEN + 1];
+#pragma unroll
+              for (int b = 0; b < NEN; b += 2) {
+                const uint32_t w2 = eo[(a * NEN + b) / 2];
+                p[b] = win + (int)(w2 & 0xFFFFu) * r.neqs + q;
+                p[b + 1] = win + (int)(w2 >> 16) * r.neqs + q;
+                add[b] = Am[rho][b / 2].x + Dh[rho][b / 2].x;
+                add[b + 1] = Am[rho][b / 2].y + Dh[rho][b / 2].y;
+              }
+              p[NEN] = win + (int)ro * r.neqs + q;
+              add[NEN] = (rho & 1) ? bv2[rho / 2].y : bv2[rho / 2].x;
+              float old[NEN + 1];
+#pragma unroll
+              for (int b = 0; b <= NEN; ++b) old[b] = *p[b];
+#pragma unroll
+              for (int b = 0; b <= NEN; ++b) *p[b] = old[b] + add[b];
+            }
+          }
+          __syncthreads();
+        }
+      }
+      if (t + 2 < t1) stage_plan<NT>(r, t + 2, S);
+      cp_async_commit();
+    }
+    __syncthreads();
+    flush_rows(r, win, t1 - 1, warp, NT / 32);
     __syncthreads();
   }
 }

@@ -20,7 +20,7 @@ FEA_F64_PLAIN, FEA_F32_FUSED = 0, 1
 FEA_TERM_MASS, FEA_TERM_CONV, FEA_TERM_DIFF, FEA_TERM_REAC, FEA_TERM_SUPG, FEA_TERM_ALL = 1, 2, 4, 8, 16, 31
 FEA_SCATTER_AUTO, FEA_SCATTER_ATOMIC, FEA_SCATTER_ROWOWNED, FEA_SCATTER_GATHER = 0, 1, 2, 3
 FEA_CONTRACT_AUTO, FEA_CONTRACT_CUDA, FEA_CONTRACT_TC_BF16X3, FEA_CONTRACT_TC_TF32X3 = 0, 1, 2, 3
-FEA_MAP_AUTO, FEA_MAP_TYPE_KERNEL, FEA_MAP_WARP_PER_ELEMENT = 0, 1, 2
+FEA_MAP_AUTO, FEA_MAP_TYPE_KERNEL, FEA_MAP_WARP_PER_ELEMENT, FEA_MAP_TWO_THREADS_PER_ITEM = 0, 1, 2, 3
 STATUS = {0: "FEA_OK", 1: "FEA_ERR_ARG", 2: "FEA_ERR_RANGE", 3: "FEA_ERR_DUP_NODE", 4: "FEA_ERR_INVERTED",
           5: "FEA_ERR_TOO_LARGE", 6: "FEA_ERR_OOM", 7: "FEA_ERR_CUDA", 8: "FEA_ERR_TIMEOUT", 9: "FEA_ERR_STATE"}
 NEN = {FEA_TET4: 4, FEA_HEX8: 8, FEA_HEX27: 27, FEA_PEN6: 6, FEA_PYR5: 5}

@@ -179,7 +179,7 @@ def test_tuning_options_arguments():
     w = G.make_workload(2, n=2, n_eq=1)
     run = GpuRun(w.mesh)
     try:
-        for kw in (dict(mapping=3), dict(elems_per_cta=-1), dict(elems_per_cta=1000)):
+        for kw in (dict(mapping=4), dict(elems_per_cta=-1), dict(elems_per_cta=1000)):
             with pytest.raises(fea.FeaError) as e:
                 run.assemble(w.fields, fea.FEA_F32_FUSED, **kw)
             assert e.value.code == 1
