@@ -28,14 +28,25 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
   const float inv_dt = (float)(1.0 / p.dt);
   const bool t_mass = p.terms & FEA_TERM_MASS, t_conv = p.terms & FEA_TERM_CONV, t_diff = p.terms & FEA_TERM_DIFF,
              t_reac = p.terms & FEA_TERM_REAC, t_supg = p.terms & FEA_TERM_SUPG;
+  // 16-byte loads of an element's connectivity and position rows, when the block's arrays start
+  // 16-byte aligned (a Tet4 block after blocks of other types may not)
+  const bool vec = ((reinterpret_cast<uintptr_t>(p.conn) | reinterpret_cast<uintptr_t>(p.pos)) & 15) == 0;
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < items;
        it += (int64_t)gridDim.x * blockDim.x) {
     const int64_t eo = it / p.eq_count;
     const int qq = (int)(it - eo * p.eq_count), q = p.eq0 + qq;
     const int64_t e = p.elem_order ? (int64_t)__ldg(p.elem_order + eo) : eo;
     int32_t n[4];
+    if (vec) {
+      const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.conn) + e);  // conn [E][4]: 16-byte rows
+      n[0] = c4.x;
+      n[1] = c4.y;
+      n[2] = c4.z;
+      n[3] = c4.w;
+    } else {
 #pragma unroll
-    for (int a = 0; a < 4; ++a) n[a] = __ldg(p.conn + e * 4 + a);
+      for (int a = 0; a < 4; ++a) n[a] = __ldg(p.conn + e * 4 + a);
+    }
     float J[3][3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -161,11 +172,15 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
       }
     } else {
       float* vq = p.values + (int64_t)q * p.nnz;
-      const int32_t* pe = p.pos + e * 16;
+      const int32_t* pe = p.pos + e * 16;  // pos [E][4][4]
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) atomicAdd(vq + __ldg(pe + a * 4 + c), A[a][c]);
+        const int4 k4 = vec ? __ldg(reinterpret_cast<const int4*>(pe) + a)
+                            : make_int4(__ldg(pe + 4 * a), __ldg(pe + 4 * a + 1), __ldg(pe + 4 * a + 2), __ldg(pe + 4 * a + 3));
+        atomicAdd(vq + k4.x, A[a][0]);
+        atomicAdd(vq + k4.y, A[a][1]);
+        atomicAdd(vq + k4.z, A[a][2]);
+        atomicAdd(vq + k4.w, A[a][3]);
         atomicAdd(p.rhs + fo + n[a], b[a]);
       }
     }
