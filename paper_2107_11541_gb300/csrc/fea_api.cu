@@ -433,6 +433,7 @@ static AsmArgs<T> make_args(fea_mesh* m, const fea_pattern* p, const void* vel, 
   a.kappa_threshold = o->kappa_threshold;
   a.status = m->status;
   a.elem_order = (!m->mixed && m->type == FEA_TET4) ? p->elem_order : nullptr;
+  a.t4_rows = (!m->mixed && m->type == FEA_TET4) ? p->t4_rows : nullptr;
   a.contraction = o->contraction == FEA_CONTRACT_AUTO ? FEA_CONTRACT_CUDA : o->contraction;
   a.mapping = o->mapping == FEA_MAP_AUTO ? FEA_MAP_TYPE_KERNEL : o->mapping;
   a.batch = o->elems_per_cta;
@@ -1042,6 +1043,7 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->lumped[1]);
   cudaFree(p->rk_ws);
   cudaFree(p->elem_order);
+  cudaFree(p->t4_rows);
   cudaFree(p->hex8_fnode);
   for (auto& kv : p->cancel) {
     cudaFree(kv.second.rows);
@@ -1144,6 +1146,8 @@ fea_status fea_pattern_build(fea_mesh* m, fea_pattern** out) {
   if (st != FEA_OK) return done(st);
   if (!m->mixed && m->type == FEA_TET4) {  // the thread-per-item Tet4 kernel walks elements in this order
     st = element_order(m, &p->elem_order);
+    if (st == FEA_OK) st = tet4_rows(m, p->elem_order, p->pos, &p->t4_rows);
+    if (st == FEA_OK) st = fea_sync(m);
     if (st != FEA_OK) return done(st);
   }
   st = plan_build(m, p, &p->plan);

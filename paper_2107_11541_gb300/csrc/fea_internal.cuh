@@ -119,8 +119,10 @@ struct fea_pattern {
   // device workspace for fea_assemble_host
   void* ws;
   size_t ws_bytes;
-  // locality order of the elements (Tet4 meshes; null otherwise)
+  // locality order of the elements (Tet4 meshes; null otherwise), and per element in that
+  // order its 4 node ids and 16 CSR positions as one 80-byte record
   int32_t* elem_order;
+  int32_t* t4_rows;
   // fea_pcg: diagonal position of every row, and the solver's vectors and scalars
   int32_t* diag;
   void* pcg_ws;
@@ -305,6 +307,7 @@ template <typename T>
 struct AsmArgs {
   const int32_t* conn;
   const int32_t* elem_order = nullptr;  // Tet4 atomic kernel: element visit order (null: 0, 1, ...)
+  const int32_t* t4_rows = nullptr;     // Tet4: [E][20] node ids and positions of the elements in that order
   const double* coords;  // [N][3]
   const float* xhi;      // [3][N]
   const float* xlo;      // [3][N]
@@ -366,6 +369,9 @@ fea_status launch_hex27_f32(const AsmArgs<float>& a, cudaStream_t s);
 // Morton order of the element centroids (device array of n_elem ids, owned by the caller; null
 // for meshes of several types or fewer than two elements).  Waits for the mesh's stream.
 fea_status element_order(const fea_mesh* m, int32_t** out);
+// Per element in the given order (null: element order 0, 1, ... as element_order returns for
+// meshes of fewer than 2 elements), its 4 node ids and 16 CSR positions ([E][20] int32).
+fea_status tet4_rows(const fea_mesh* m, const int32_t* order, const int32_t* pos, int32_t** out);
 // y_q = A_q x_q for the n_eq FP32 matrices on pattern p (overwrite or add), on stream s.
 fea_status launch_spmv_f32(const fea_pattern* p, const float* values, const float* x, float* y, int n_eq,
                            bool accumulate, cudaStream_t s);

@@ -128,4 +128,37 @@ fea_status element_order(const fea_mesh* m, int32_t** out) {
   return done(FEA_OK);
 }
 
+namespace {
+__global__ void k_tet4_rows(const int32_t* __restrict__ order, const int32_t* __restrict__ conn,
+                            const int32_t* __restrict__ pos, int64_t n_elem, int32_t* __restrict__ out) {
+  const int64_t total = n_elem * 20;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = i / 20, j = i - k * 20, e = order ? (int64_t)order[k] : k;  // no order: the given one
+    out[i] = j < 4 ? conn[e * 4 + j] : pos[e * 16 + (j - 4)];
+  }
+}
+}  // namespace
+
+fea_status tet4_rows(const fea_mesh* m, const int32_t* order, const int32_t* pos, int32_t** out) {
+  *out = nullptr;
+  const int64_t E = m->n_elem;
+  if (E == 0) return FEA_OK;
+  int32_t* rows = nullptr;
+  if (cudaMalloc(&rows, sizeof(int32_t) * 20 * (size_t)E) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(FEA_ERR_OOM, "Tet4 element rows: %lld bytes", (long long)(80 * E));
+  }
+  const int64_t total = 20 * E;
+  k_tet4_rows<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, m->stream>>>(order, m->conn, pos,
+                                                                                                  E, rows);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cudaFree(rows);
+    return fail(FEA_ERR_CUDA, "Tet4 element rows: %s", cudaGetErrorString(e));
+  }
+  count_launches(1);
+  *out = rows;
+  return FEA_OK;
+}
+
 }  // namespace fea

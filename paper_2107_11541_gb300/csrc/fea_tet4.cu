@@ -11,7 +11,9 @@
 // to the gather scratch.  Gauss points of badly conditioned elements (condition estimate
 // above the threshold, or det <= 0 in FP32) get J^-1 from the FP64 coordinates.  Elements
 // are visited in the pattern's Morton order of their centroids, so that the lanes of a warp
-// hold neighbouring elements and their atomics land on few rows.
+// hold neighbouring elements and their atomics land on few rows; the pattern keeps each
+// element's node ids and CSR positions in that order too, as 80-byte records, so that a warp's
+// loads of them are contiguous.
 #include <algorithm>
 
 #include "fea_internal.cuh"
@@ -37,7 +39,14 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
     const int qq = (int)(it - eo * p.eq_count), q = p.eq0 + qq;
     const int64_t e = p.elem_order ? (int64_t)__ldg(p.elem_order + eo) : eo;
     int32_t n[4];
-    if (vec) {
+    const int4* rec = p.t4_rows ? reinterpret_cast<const int4*>(p.t4_rows) + eo * 5 : nullptr;  // 80-byte record
+    if (rec) {
+      const int4 c4 = __ldg(rec);
+      n[0] = c4.x;
+      n[1] = c4.y;
+      n[2] = c4.z;
+      n[3] = c4.w;
+    } else if (vec) {
       const int4 c4 = __ldg(reinterpret_cast<const int4*>(p.conn) + e);  // conn [E][4]: 16-byte rows
       n[0] = c4.x;
       n[1] = c4.y;
@@ -175,8 +184,10 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
       const int32_t* pe = p.pos + e * 16;  // pos [E][4][4]
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
-        const int4 k4 = vec ? __ldg(reinterpret_cast<const int4*>(pe) + a)
-                            : make_int4(__ldg(pe + 4 * a), __ldg(pe + 4 * a + 1), __ldg(pe + 4 * a + 2), __ldg(pe + 4 * a + 3));
+        const int4 k4 = rec   ? __ldg(rec + 1 + a)
+                        : vec ? __ldg(reinterpret_cast<const int4*>(pe) + a)
+                              : make_int4(__ldg(pe + 4 * a), __ldg(pe + 4 * a + 1), __ldg(pe + 4 * a + 2),
+                                          __ldg(pe + 4 * a + 3));
         atomicAdd(vq + k4.x, A[a][0]);
         atomicAdd(vq + k4.y, A[a][1]);
         atomicAdd(vq + k4.z, A[a][2]);
