@@ -472,6 +472,11 @@ fea_status elem_f32(fea_mesh* m, fea_pattern* p, const AsmArgs<float>& a0, cudaS
     if (b.type == FEA_HEX8 && a.mapping != FEA_MAP_WARP_PER_ELEMENT) {
       if (p->plan) FEA_TRY(plan_elem(p->plan, a, s));
       else FEA_TRY(hex8_elem(p->hex8_fnode, p->hex8_fnode_bytes, a, s));
+    } else if (b.type == FEA_TET4 && !m->mixed && a.eq_count == 1 && a.mapping != FEA_MAP_WARP_PER_ELEMENT &&
+               p->t4_node) {  // one equation: node records read with three 16-byte loads per node
+      a.t4_node = p->t4_node;
+      FEA_TRY(tet4_node_records(a, p->t4_node, s));
+      FEA_TRY(launch_generic_f32(a, b.type, s));
     } else {
       FEA_TRY(launch_generic_f32(a, b.type, s));
     }
@@ -1044,6 +1049,7 @@ fea_status fea_pattern_destroy(fea_pattern* p) {
   cudaFree(p->rk_ws);
   cudaFree(p->elem_order);
   cudaFree(p->t4_rows);
+  cudaFree(p->t4_node);
   cudaFree(p->hex8_fnode);
   for (auto& kv : p->cancel) {
     cudaFree(kv.second.rows);
@@ -1147,6 +1153,10 @@ fea_status fea_pattern_build(fea_mesh* m, fea_pattern** out) {
   if (!m->mixed && m->type == FEA_TET4) {  // the thread-per-item Tet4 kernel walks elements in this order
     st = element_order(m, &p->elem_order);
     if (st == FEA_OK) st = tet4_rows(m, p->elem_order, p->pos, &p->t4_rows);
+    if (st == FEA_OK && cudaMalloc(&p->t4_node, 48 * (size_t)std::max<int64_t>(N, 1)) != cudaSuccess) {
+      cudaGetLastError();
+      p->t4_node = nullptr;  // optional: the kernel then reads the node arrays directly
+    }
     if (st == FEA_OK) st = fea_sync(m);
     if (st != FEA_OK) return done(st);
   }

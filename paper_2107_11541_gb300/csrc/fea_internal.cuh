@@ -123,6 +123,7 @@ struct fea_pattern {
   // order its 4 node ids and 16 CSR positions as one 80-byte record
   int32_t* elem_order;
   int32_t* t4_rows;
+  float4* t4_node;       // Tet4, one equation: node records rebuilt every call ([N][3])
   // fea_pcg: diagonal position of every row, and the solver's vectors and scalars
   int32_t* diag;
   void* pcg_ws;
@@ -308,6 +309,7 @@ struct AsmArgs {
   const int32_t* conn;
   const int32_t* elem_order = nullptr;  // Tet4 atomic kernel: element visit order (null: 0, 1, ...)
   const int32_t* t4_rows = nullptr;     // Tet4: [E][20] node ids and positions of the elements in that order
+  const float4* t4_node = nullptr;      // Tet4, one equation: per-call node records [N][3] (tet4_node_records)
   const double* coords;  // [N][3]
   const float* xhi;      // [3][N]
   const float* xlo;      // [3][N]
@@ -361,6 +363,9 @@ fea_status launch_generic_f64(const AsmArgs<double>& a, fea_elem_t type, cudaStr
 fea_status launch_generic_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s);
 // FP32 Tet4: one thread per (element, equation) (atomics, or the gather scratch if a.em).
 fea_status launch_tet4_f32(const AsmArgs<float>& a, cudaStream_t s);
+// The node records of the Tet4 kernel for the launch's single equation eq0: [N][3] float4 =
+// (xhi, xlo.x), (xlo.y, xlo.z, u.x, u.y), (u.z, k, s, phi_old).
+fea_status tet4_node_records(const AsmArgs<float>& a, float4* out, cudaStream_t s);
 // FP32 Pen6 / Pyr5: one thread per (element, equation) item, per-point geometry in registers.
 fea_status launch_small_f32(const AsmArgs<float>& a, fea_elem_t type, cudaStream_t s);
 // FP32 Hex27, one CTA per element, full operator and up to 12 equations (hex27_kernel_applies).

@@ -56,15 +56,47 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
 #pragma unroll
       for (int a = 0; a < 4; ++a) n[a] = __ldg(p.conn + e * 4 + a);
     }
+    // node data: coordinates (float hi/lo), velocity and the equation's k, s, phi_old, from the
+    // per-call node records (one equation: 48 bytes per node, three 16-byte loads) or the arrays
+    float xh[4][3], xl[4][3], un[4][3], kn[4], sn[4], pn[4];
+    const int64_t fo = (int64_t)q * N;
+    if (p.t4_node) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const float4* r = p.t4_node + (int64_t)n[a] * 3;
+        const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2);
+        xh[a][0] = r0.x;
+        xh[a][1] = r0.y;
+        xh[a][2] = r0.z;
+        xl[a][0] = r0.w;
+        xl[a][1] = r1.x;
+        xl[a][2] = r1.y;
+        un[a][0] = r1.z;
+        un[a][1] = r1.w;
+        un[a][2] = r2.x;
+        kn[a] = r2.y;
+        sn[a] = r2.z;
+        pn[a] = r2.w;
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          xh[a][i] = __ldg(p.xhi + (int64_t)i * N + n[a]);
+          xl[a][i] = __ldg(p.xlo + (int64_t)i * N + n[a]);
+          un[a][i] = __ldg(p.vel + (int64_t)i * N + n[a]);
+        }
+        kn[a] = __ldg(p.kd + fo + n[a]);
+        sn[a] = __ldg(p.sr + fo + n[a]);
+        pn[a] = __ldg(p.phi + fo + n[a]);
+      }
+    }
     float J[3][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const float* hi = p.xhi + (int64_t)i * N;
-      const float* lo = p.xlo + (int64_t)i * N;
-      const float h0 = __ldg(hi + n[0]), l0 = __ldg(lo + n[0]);
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
-      for (int j = 0; j < 3; ++j) J[i][j] = (__ldg(hi + n[j + 1]) - h0) + (__ldg(lo + n[j + 1]) - l0);
-    }
+      for (int j = 0; j < 3; ++j) J[i][j] = (xh[j + 1][i] - xh[0][i]) + (xl[j + 1][i] - xl[0][i]);
     float det = det3(J), G[3][3];
     inv_transpose3(J, det, G);
     float nj = 0.f, ni = 0.f;
@@ -94,16 +126,6 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
       gr[2][i] = G[i][1];
       gr[3][i] = G[i][2];
       gr[0][i] = -(G[i][0] + G[i][1] + G[i][2]);
-    }
-    float un[4][3], kn[4], sn[4], pn[4];
-    const int64_t fo = (int64_t)q * N;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) un[a][i] = __ldg(p.vel + (int64_t)i * N + n[a]);
-      kn[a] = __ldg(p.kd + fo + n[a]);
-      sn[a] = __ldg(p.sr + fo + n[a]);
-      pn[a] = __ldg(p.phi + fo + n[a]);
     }
     const float dv = det * (1.0f / 24.0f);  // w_g det J, the same at every point
     const float h = cbrtf(4.0f * dv);       // V_e^(1/3), V_e = sum_g dv
@@ -198,7 +220,29 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
   }
 }
 
+// Per-call node records of one equation: xhi, xlo, u, k, s, phi_old as three float4 per node.
+__global__ void k_t4_nodes(const float* __restrict__ xhi, const float* __restrict__ xlo, const float* __restrict__ vel,
+                           const float* __restrict__ kd, const float* __restrict__ sr, const float* __restrict__ phi,
+                           int64_t n_node, float4* __restrict__ out) {
+  for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < n_node; n += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t N = n_node;
+    out[3 * n] = make_float4(xhi[n], xhi[N + n], xhi[2 * N + n], xlo[n]);
+    out[3 * n + 1] = make_float4(xlo[N + n], xlo[2 * N + n], vel[n], vel[N + n]);
+    out[3 * n + 2] = make_float4(vel[2 * N + n], kd[n], sr[n], phi[n]);
+  }
+}
+
 }  // namespace
+
+fea_status tet4_node_records(const AsmArgs<float>& a, float4* out, cudaStream_t s) {
+  if (a.n_node == 0) return FEA_OK;
+  const int64_t fo = (int64_t)a.eq0 * a.n_node;
+  k_t4_nodes<<<(unsigned)std::min<int64_t>((a.n_node + 255) / 256, 152 * 16), 256, 0, s>>>(
+      a.xhi, a.xlo, a.vel, a.kd + fo, a.sr + fo, a.phi + fo, a.n_node, out);
+  FEA_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return FEA_OK;
+}
 
 fea_status launch_tet4_f32(const AsmArgs<float>& a, cudaStream_t s) {
   const int64_t items = a.n_elem * a.eq_count;
