@@ -186,8 +186,9 @@ def profiled_traffic(workload: str):
 
 
 def make(workload: str, n=None):
-    """The named workload; ``n`` shrinks it to n cells per axis (profiling captures only)."""
-    return G.make_workload(WORKLOADS[workload], n=n)
+    """The named workload with FP32 fields (the values the FP32 path consumes; the oracle widens
+    them); ``n`` shrinks it to n cells per axis (profiling captures only)."""
+    return G.make_workload(WORKLOADS[workload], n=n, dtype=np.float32)
 
 
 def cpu_oracle_sample(w, budget_s: float):
@@ -418,7 +419,7 @@ def main():
     h = fea.fea_mesh_create(m.coords, m.conn, m.elem_type, stream)
     p = fea.fea_pattern_build(h)
     nnz = fea.fea_pattern_get(p)[3]
-    f32 = fld.astype(np.float32)
+    f32 = fld if fld.diffusivity.dtype == np.float32 else fld.astype(np.float32)
     with torch.cuda.stream(stream):
         dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda(non_blocking=False)
                for a in (f32.velocity, f32.diffusivity, f32.reaction, f32.phi_old)]
@@ -622,7 +623,7 @@ def main():
 
     if not args.no_f64 and rank == 0:
         q64 = q if m.n_elem * q <= 60_000_000 else 4
-        d64 = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        d64 = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
                for a in (fld.velocity, fld.diffusivity[:q64], fld.reaction[:q64], fld.phi_old[:q64])]
         del values
         v64 = torch.empty((q64, nnz), dtype=torch.float64, device="cuda")
@@ -684,7 +685,7 @@ def side_workload(name: str, steps: int, warmup: int, parity: bool):
     h = fea.fea_mesh_create(m.coords, m.conn, m.elem_type, stream)
     p = fea.fea_pattern_build(h)
     nnz = fea.fea_pattern_get(p)[3]
-    f32 = fld.astype(np.float32)
+    f32 = fld if fld.diffusivity.dtype == np.float32 else fld.astype(np.float32)
     with torch.cuda.stream(stream):
         dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (f32.velocity, f32.diffusivity,
                                                                           f32.reaction, f32.phi_old)]
@@ -725,7 +726,7 @@ def side_workload(name: str, steps: int, warmup: int, parity: bool):
         res["parity"] = sampled_parity(w, values, rhs, p, nnz)
     del values
     q64 = q if m.n_elem * q <= 60_000_000 else 4
-    d64 = [torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    d64 = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
            for a in (fld.velocity, fld.diffusivity[:q64], fld.reaction[:q64], fld.phi_old[:q64])]
     v64 = torch.empty((q64, nnz), dtype=torch.float64, device="cuda")
     r64 = torch.empty((q64, m.n_node), dtype=torch.float64, device="cuda")
@@ -804,7 +805,7 @@ def run_mixed(args, rank, world, local):
     h = fea.fea_mesh_create_mixed(mm.coords, mm.blocks, stream)
     p = fea.fea_pattern_build(h)
     r_, c_, _, nnz = fea.fea_pattern_get(p)
-    f32 = fld.astype(np.float32)
+    f32 = fld if fld.diffusivity.dtype == np.float32 else fld.astype(np.float32)
     with torch.cuda.stream(stream):
         dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (f32.velocity, f32.diffusivity,
                                                                           f32.reaction, f32.phi_old)]
@@ -961,10 +962,11 @@ def end_to_end(h, p, f32, m, nnz, q, stream, steps, world, dist, values_dev=None
     import torch
     from paper_2107_11541_gb300 import fea
     need = 4 * (f32.velocity.size + f32.diffusivity.size + f32.reaction.size + f32.phi_old.size + q * (nnz + m.n_node))
+    local = int(os.environ.get("LOCAL_WORLD_SIZE", world))  # ranks on this host, each pinning its own buffers
     avail = host_memory_available()
-    if need > 0.6 * avail:  # pinned host buffers this large would crowd the host
-        return {"skipped": f"the pinned host buffers ({need / 1e9:.1f} GB) exceed 60% of the host memory "
-                           f"available to this process ({avail / 1e9:.1f} GB)"}
+    if need * local > 0.6 * avail:  # pinned host buffers this large would crowd the host
+        return {"skipped": f"the pinned host buffers ({need / 1e9:.1f} GB per rank, {local} ranks on this host) "
+                           f"exceed 60% of the host memory available ({avail / 1e9:.1f} GB)"}
     pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
            for a in (f32.velocity, f32.diffusivity, f32.reaction, f32.phi_old)]
     hv = torch.empty((q, nnz), dtype=torch.float32).pin_memory()

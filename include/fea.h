@@ -139,8 +139,9 @@ typedef struct {
   int32_t terms;            /* bit mask of FEA_TERM_*, default FEA_TERM_ALL */
   int32_t scatter;          /* fea_scatter, default FEA_SCATTER_AUTO */
   int32_t accumulate;       /* 0: overwrite values/rhs (default); 1: add to them */
-  double kappa_threshold;   /* F32 path: elements whose Jacobian condition estimate exceeds this get FP64
-                               geometry (default 1e3) */
+  double kappa_threshold;   /* F32 path: Gauss points whose Jacobian condition estimate |J|_F |J^-1|_F (an
+                               upper bound of the 2-norm condition number, 3 for a scaled identity)
+                               exceeds this get FP64 geometry (default 1e3) */
   void* event_begin;        /* optional cudaEvent_t recorded on the mesh stream just before the assembly
                                kernel(s), after any output zeroing; NULL = none */
   void* event_end;          /* optional cudaEvent_t recorded just after the assembly kernel(s) */

@@ -100,7 +100,8 @@ __device__ TC warp_geometry(const AsmArgs<TI>& p, int64_t e, TC* S, const TC* Nt
     TC G[3][3];
     inv_transpose3(J, det, G);
     if constexpr (sizeof(TC) == 4) {
-      // condition estimate |J|_F |J^-1|_F / 3; above the threshold (or det <= 0 in FP32) det and
+      // condition estimate |J|_F |J^-1|_F (an upper bound of the 2-norm condition number); above the
+      // threshold (or det <= 0 in FP32) det and
       // J^-1 are redone in FP64 from the FP64 coordinates
       TC nj = 0, ni = 0;
       for (int i = 0; i < 3; ++i)
@@ -108,7 +109,7 @@ __device__ TC warp_geometry(const AsmArgs<TI>& p, int64_t e, TC* S, const TC* Nt
           nj += J[i][j] * J[i][j];
           ni += G[i][j] * G[i][j];
         }
-      if (!(det > TC(0)) || !(nj * ni <= TC(9) * (TC)(p.kappa_threshold * p.kappa_threshold))) {
+      if (!(det > TC(0)) || !(nj * ni <= (TC)(p.kappa_threshold * p.kappa_threshold))) {
         double Jd[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Gd[3][3];
         for (int a = 0; a < NEN; ++a) {
           double Nd, dNd[3];

@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(H27_THREADS, 1) k_hex27(AsmArgs<float> p) {
           nj = fmaf(J[i][j], J[i][j], nj);
           ni = fmaf(G[i][j], G[i][j], ni);
         }
-      if (!(det > 0.f) || !(nj * ni <= 9.0f * (float)(p.kappa_threshold * p.kappa_threshold))) {
+      if (!(det > 0.f) || !(nj * ni <= (float)(p.kappa_threshold * p.kappa_threshold))) {
         double xid[3], w;
         gauss_point<FEA_HEX27>(g, xid, w);
         double Jd[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Gd[3][3];

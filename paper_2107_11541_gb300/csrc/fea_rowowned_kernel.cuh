@@ -217,7 +217,8 @@ __device__ __forceinline__ void geometry(const RoArgs& r, const Stage& S, float*
     }
     float det = det3(J), Gt[3][3];
     inv_transpose3(J, det, Gt);
-    // condition estimate |J|_F |J^-1|_F / 3; above the threshold the Jacobian is redone in FP64
+    // condition estimate |J|_F |J^-1|_F (an upper bound of the 2-norm condition number); above the
+    // threshold the Jacobian is redone in FP64
     float nj = 0.f, ni = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
@@ -226,7 +227,7 @@ __device__ __forceinline__ void geometry(const RoArgs& r, const Stage& S, float*
         nj = fmaf(J[i][j], J[i][j], nj);
         ni = fmaf(Gt[i][j], Gt[i][j], ni);
       }
-    if (!(det > 0.f) || nj * ni > 9.0f * (float)(A_.kappa_threshold * A_.kappa_threshold)) {
+    if (!(det > 0.f) || nj * ni > (float)(A_.kappa_threshold * A_.kappa_threshold)) {
       const int32_t* ids = S.nid + ge * NEN;
       const double pd = 0.57735026918962576451;
       const double xid[3] = {(g & 1) ? pd : -pd, (g & 2) ? pd : -pd, (g & 4) ? pd : -pd};

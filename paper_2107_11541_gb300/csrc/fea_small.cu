@@ -43,7 +43,7 @@ __device__ __forceinline__ float point_inverse(const AsmArgs<float>& p, const fl
       nj = fmaf(J[i][j], J[i][j], nj);
       ni = fmaf(G[i][j], G[i][j], ni);
     }
-  if (!(det > 0.f) || !(nj * ni <= 9.0f * (float)(p.kappa_threshold * p.kappa_threshold))) {
+  if (!(det > 0.f) || !(nj * ni <= (float)(p.kappa_threshold * p.kappa_threshold))) {
     double xid[3], w, Jd[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, Gd[3][3];
     gauss_point<TYPE>(g, xid, w);
     for (int a = 0; a < NEN; ++a) {

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) k_tet4_f32(AsmArgs<float> p) {
         nj = fmaf(J[i][j], J[i][j], nj);
         ni = fmaf(G[i][j], G[i][j], ni);
       }
-    if (!(det > 0.f) || !(nj * ni <= 9.0f * (float)(p.kappa_threshold * p.kappa_threshold))) {
+    if (!(det > 0.f) || !(nj * ni <= (float)(p.kappa_threshold * p.kappa_threshold))) {
       double Jd[3][3], Gd[3][3];
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) Jd[i][j] = p.coords[(int64_t)n[j + 1] * 3 + i] - p.coords[(int64_t)n[0] * 3 + i];

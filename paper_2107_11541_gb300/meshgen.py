@@ -260,16 +260,18 @@ def velocity_field(coords: np.ndarray) -> np.ndarray:
 
 
 def draw_fields(rng: np.random.Generator, coords: np.ndarray, n_eq: int, s_max: float,
-                dt: float = DT) -> Fields:
+                dt: float = DT, dtype=np.float64) -> Fields:
+    """The seeded nodal fields; dtype=float32 rounds each draw as it is made (the same values as
+    drawing in float64 and rounding afterwards, without the float64 arrays)."""
     n = coords.shape[0]
-    k = np.empty((n_eq, n))
-    s = np.empty((n_eq, n))
-    p = np.empty((n_eq, n))
+    k = np.empty((n_eq, n), dtype=dtype)
+    s = np.empty((n_eq, n), dtype=dtype)
+    p = np.empty((n_eq, n), dtype=dtype)
     for q in range(n_eq):
         k[q] = rng.lognormal(-4.0, 0.5, size=n)
         s[q] = rng.uniform(0.0, s_max, size=n)
         p[q] = rng.uniform(0.0, 1.0, size=n)
-    return Fields(velocity_field(coords), k, s, p, dt)
+    return Fields(velocity_field(coords).astype(dtype), k, s, p, dt)
 
 
 def step_params(n_steps: int, n_eq: int, seed: int = SEED_BASE + 1000) -> np.ndarray:
@@ -308,11 +310,12 @@ CONFIGS = {
 
 
 def make_workload(index: int, n: int | None = None, n_eq: int | None = None, seed: int | None = None,
-                  stretched_slab: bool = False) -> Workload:
+                  stretched_slab: bool = False, dtype=np.float64) -> Workload:
     """Build workload ``index`` (optionally shrunk: ``n`` cells per axis, ``n_eq`` equations).
 
     ``stretched_slab`` compresses the middle layer of cells in z to 1e-4 of its width
     (aspect ratio 1e4), which makes the Jacobians of that layer badly conditioned.
+    ``dtype`` is the dtype of the fields (float32: the values the FP32 path consumes).
     """
     cfg = dict(CONFIGS[index])
     if n is not None:
@@ -320,7 +323,7 @@ def make_workload(index: int, n: int | None = None, n_eq: int | None = None, see
     if n_eq is not None:
         cfg["n_eq"] = n_eq
     mesh, rng = _workload_mesh(index, cfg, seed, stretched_slab)
-    fields = draw_fields(rng, mesh.coords, cfg["n_eq"], cfg["s_max"])
+    fields = draw_fields(rng, mesh.coords, cfg["n_eq"], cfg["s_max"], dtype=dtype)
     return Workload(cfg["name"] if n is None and n_eq is None else f"{cfg['name']}_n{mesh.n_cells}_q{cfg['n_eq']}",
                     mesh, fields, cfg["precision"])
 

@@ -29,12 +29,12 @@ def rotated_slab(cfg, n, q):
     return w.mesh, w.fields
 
 
-def rotated_layer_slab(t, n, q):
-    """Elements of type t on an n^3 grid whose middle z layer of cells is 1e-4 as thick as the
+def rotated_layer_slab(t, n, q, ratio=1e-4):
+    """Elements of type t on an n^3 grid whose middle z layer of cells is `ratio` as thick as the
     others (prisms: triangles in the y-z planes; pyramids: six per cell around its centre;
     tetrahedra: the Kuhn split), rotated off the axes."""
     widths = np.ones(n)
-    widths[n // 2] = 1e-4
+    widths[n // 2] = ratio
     widths /= widths.sum()
     faces = np.concatenate([[0.0], np.cumsum(widths)])
     faces[-1] = 1.0
@@ -81,3 +81,12 @@ def test_kappa_fallback_keeps_fp32_parity(cfg, n, q, scatter):
 def test_kappa_fallback_other_types(t, scatter):
     mesh, fields = rotated_layer_slab(t, 5, 2)
     check_fallback(mesh, fields, 2, scatter)
+
+
+def test_condition_just_above_threshold_takes_fp64():
+    """A Hex8 layer 1/1500 as thick as its neighbours: the Jacobians' 2-norm condition number is
+    about 1500, just above the 1e3 threshold, while |J|_F |J^-1|_F / 3 would read about 700.
+    The estimate compared is the upper bound |J|_F |J^-1|_F, so these points take FP64 geometry
+    and the result meets the FP32 tolerance; the fallback matters here (it is worse without)."""
+    mesh, fields = rotated_layer_slab(G.HEX8, 5, 2, ratio=1.0 / 1500.0)
+    check_fallback(mesh, fields, 2, fea.FEA_SCATTER_GATHER)
