@@ -104,13 +104,11 @@ __device__ __forceinline__ void stage_nodes(const RoArgs& r, int t, const Stage&
 }
 
 // Writes the rows completed by batch tb to HBM and clears their slots; warp w of nw takes a
-// contiguous share of the batch's records, which the plan sorts by row.  Consecutive rows r,
-// r+1, ... have consecutive CSR ranges, so a run of them is one contiguous segment of every
-// equation's values (and of its RHS).  The warp reads 32 records at a time (one per lane),
-// splits them into runs, and writes each run per equation in chunks of 32 consecutive CSR
-// positions (one store instruction per chunk), each lane finding the row of its position by a
-// binary search over the run's records; the run's RHS entries are one store per equation.
-// The stores are plain: every value is written once.  Accumulating calls add row by row.
+// contiguous share of the batch's records.  Row by row, lane c holds column c: it loads 8
+// equations' values (consecutive words of the slot) before storing them, so one store
+// instruction writes one equation's row segment (consecutive CSR positions); the row's RHS is one
+// store with the lanes over the equations.  Every value is written once (plain stores;
+// accumulating calls add).
 __device__ __forceinline__ void flush_rows(const RoArgs& r, float* win, int tb, int w0, int nw) {
   const AsmArgs<float>& A_ = r.a;
   const int lane = threadIdx.x & 31, n_eq = A_.eq_count;
@@ -118,74 +116,41 @@ __device__ __forceinline__ void flush_rows(const RoArgs& r, float* win, int tb, 
   const int f0 = fb + (int)(((int64_t)nb * w0) / nw), nf = fb + (int)(((int64_t)nb * (w0 + 1)) / nw) - f0;
   float* const values = A_.values + (int64_t)A_.eq0 * A_.nnz;
   float* const rhs = A_.rhs + (int64_t)A_.eq0 * A_.n_node;
+  const bool acc = r.accumulate != 0;
+  constexpr int QG = 8;
   for (int f = 0; f < nf; f += 32) {
     const int nr = min(32, nf - f);
-    int4 rec = make_int4(-2, 0, 0, 0);
+    int4 rec = make_int4(0, 0, 0, 0);
     if (lane < nr) rec = __ldg(r.flush_meta + f0 + f + lane);
-    const int row = rec.x, base = rec.y, len = rec.w;
-    const uint32_t k0 = (uint32_t)rec.z;  // first CSR position of the row (nnz < 2^31)
-    if (!r.accumulate) {
-      const int prev = __shfl_up_sync(0xffffffffu, row, 1);
-      unsigned starts = __ballot_sync(0xffffffffu, lane < nr && (lane == 0 || row != prev + 1));
-      while (starts) {
-        const int i0 = __ffs(starts) - 1;
-        starts &= starts - 1;
-        const int i1 = starts ? __ffs(starts) - 1 : nr;  // the run: records i0 .. i1 - 1
-        const uint32_t rk0 = __shfl_sync(0xffffffffu, k0, i0);
-        const uint32_t rend = __shfl_sync(0xffffffffu, k0 + (uint32_t)len, i1 - 1);
-        const int row0 = __shfl_sync(0xffffffffu, row, i0);
-        for (uint32_t c0 = rk0 & ~31u; c0 < rend; c0 += 32) {
-          const uint32_t pos = c0 + (uint32_t)lane;
-          const bool act = pos >= rk0 && pos < rend;
-          int ri = i0;  // the last record of the run whose first position is <= pos
+    for (int i = 0; i < nr; ++i) {
+      const int row = __shfl_sync(0xffffffffu, rec.x, i), rb = __shfl_sync(0xffffffffu, rec.y, i);
+      const int64_t k0 = (uint32_t)__shfl_sync(0xffffffffu, rec.z, i);  // first CSR position (nnz < 2^31)
+      const int len = __shfl_sync(0xffffffffu, rec.w, i);
+      for (int c = lane; c < len; c += 32) {
+        const float* src = win + (rb + c) * r.neqs;
+        float* dst = values + k0 + c;
+        for (int q0 = 0; q0 < n_eq; q0 += QG) {
+          float v[QG];
 #pragma unroll
-          for (int st = 16; st >= 1; st >>= 1) {
-            const int cand = ri + st;
-            const uint32_t kc = __shfl_sync(0xffffffffu, k0, cand < 32 ? cand : 31);
-            if (cand < i1 && kc <= pos) ri = cand;
-          }
-          const int rb = __shfl_sync(0xffffffffu, base, ri);
-          const uint32_t rk = __shfl_sync(0xffffffffu, k0, ri);
-          if (act) {
-            const float* src = win + (rb + (int)(pos - rk)) * r.neqs;
-            float* dst = values + pos;
-            for (int q0 = 0; q0 < n_eq; q0 += 8) {
-              float v[8];
+          for (int k = 0; k < QG; ++k) v[k] = q0 + k < n_eq ? src[q0 + k] : 0.f;
 #pragma unroll
-              for (int k = 0; k < 8; ++k) v[k] = q0 + k < n_eq ? src[q0 + k] : 0.f;
-#pragma unroll
-              for (int k = 0; k < 8; ++k)
-                if (q0 + k < n_eq) dst[(int64_t)(q0 + k) * A_.nnz] = v[k];
+          for (int k = 0; k < QG; ++k)
+            if (q0 + k < n_eq) {
+              float* d = dst + (int64_t)(q0 + k) * A_.nnz;
+              *d = acc ? *d + v[k] : v[k];
             }
-          }
         }
-        // the run's RHS entries: rows row0 .. row0 + (i1 - i0) - 1, lane l takes record i0 + l
-        const int rbl = __shfl_sync(0xffffffffu, base, min(i0 + lane, 31));
-        if (lane < i1 - i0) {
-          const float* src = win + (rbl + r.maxcol) * r.neqs;
-          float* dst = rhs + row0 + lane;
-          for (int q = 0; q < n_eq; ++q) dst[(int64_t)q * A_.n_node] = src[q];
-        }
-        __syncwarp();
       }
-    } else {
-      for (int i = 0; i < nr; ++i) {
-        const int rrow = __shfl_sync(0xffffffffu, row, i), rb = __shfl_sync(0xffffffffu, base, i);
-        const int rlen = __shfl_sync(0xffffffffu, len, i);
-        const uint32_t rk = __shfl_sync(0xffffffffu, k0, i);
-        const int w = rlen + 1;
-        for (int idx = lane; idx < w * n_eq; idx += 32) {
-          const int q = idx / w, c = idx - q * w;
-          const float v = win[(rb + (c < rlen ? c : r.maxcol)) * r.neqs + q];
-          float* dst = c < rlen ? values + (int64_t)q * A_.nnz + rk + c : rhs + (int64_t)q * A_.n_node + rrow;
-          *dst += v;
-        }
+      const float* src = win + (rb + r.maxcol) * r.neqs;
+      for (int q = lane; q < n_eq; q += 32) {
+        float* d = rhs + (int64_t)q * A_.n_node + row;
+        *d = acc ? *d + src[q] : src[q];
       }
     }
     __syncwarp();
     // clear the slots (contiguous, 16-byte aligned: row_stride is a multiple of 4)
     for (int i = 0; i < nr; ++i) {
-      const int rb = __shfl_sync(0xffffffffu, base, i);
+      const int rb = __shfl_sync(0xffffffffu, rec.y, i);
       float4* z = reinterpret_cast<float4*>(win + rb * r.neqs);
       for (int k = lane; k < r.row_stride * r.neqs / 4; k += 32) z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
