@@ -434,19 +434,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_rowowned_hex8(RoArgs r) {
         // between two barriers.  Per matrix row the 9 words (8 columns and the RHS) are
         // distinct, so all 9 are loaded before any is stored (the compiler cannot prove that
         // and would otherwise serialise every load behind the previous store).
+        // an element's offsets: 16 bytes per matrix row (8 columns), then 16 bytes of RHS offsets
+        const uint4* eo4 = reinterpret_cast<const uint4*>(eo);
+        const uint4 rw4 = has ? eo4[NEN] : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t rws[4] = {rw4.x, rw4.y, rw4.z, rw4.w};
 #pragma unroll
         for (int rho = 0; rho < ROUNDS; ++rho) {
 #pragma unroll
           for (int a = rho; a < NEN; a += ROUNDS) {
             if (!has) break;
-            const uint32_t rw = eo[(NEN * NEN + a) / 2];
+            const uint32_t rw = rws[a / 2];
             const uint32_t ro = (a & 1) ? (rw >> 16) : (rw & 0xFFFFu);
             if (ro == NONE) continue;
+            const uint4 c4 = eo4[a];
+            const uint32_t cws[4] = {c4.x, c4.y, c4.z, c4.w};
             float* p[NEN + 1];
             float add[NEN + 1];
 #pragma unroll
             for (int b = 0; b < NEN; b += 2) {
-              const uint32_t w2 = eo[(a * NEN + b) / 2];
+              const uint32_t w2 = cws[b / 2];
               const int i0 = a <= b ? sym_index(a, b) : sym_index(b, a);
               const int i1 = a <= b + 1 ? sym_index(a, b + 1) : sym_index(b + 1, a);
               p[b] = win + (int)(w2 & 0xFFFFu) * r.neqs + q;
@@ -632,6 +638,7 @@ __global__ void __launch_bounds__(THREADS_HALF, 1) k_rowowned_hex8_half(RoArgs r
         }
         // round rho: this thread's row a = 4 H + rho (rows rho and rho + 4 of every element are
         // written in round rho, as in the one-thread kernel)
+        const uint4* eo4 = reinterpret_cast<const uint4*>(eo);  // as in k_rowowned_hex8
 #pragma unroll
         for (int rho = 0; rho < ROUNDS; ++rho) {
           if (has) {
@@ -639,11 +646,13 @@ __global__ void __launch_bounds__(THREADS_HALF, 1) k_rowowned_hex8_half(RoArgs r
             const uint32_t rw = eo[(NEN * NEN + a) / 2];
             const uint32_t ro = (a & 1) ? (rw >> 16) : (rw & 0xFFFFu);
             if (ro != NONE) {
+              const uint4 c4 = eo4[a];
+              const uint32_t cws[4] = {c4.x, c4.y, c4.z, c4.w};
               float* p[NEN + 1];
               float add[NEN + 1];
 #pragma unroll
               for (int b = 0; b < NEN; b += 2) {
-                const uint32_t w2 = eo[(a * NEN + b) / 2];
+                const uint32_t w2 = cws[b / 2];
                 p[b] = win + (int)(w2 & 0xFFFFu) * r.neqs + q;
                 p[b + 1] = win + (int)(w2 >> 16) * r.neqs + q;
                 add[b] = Am[rho][b / 2].x + Dh[rho][b / 2].x;
