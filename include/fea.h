@@ -153,7 +153,7 @@ typedef struct {
   int32_t host_parts;       /* fea_assemble_host only: the equations are assembled in this many parts,
                                each part's inputs copied in and values copied back while other parts
                                compute (at most n_eq); 0 = automatic: when the values exceed 256 MB and
-                               n_eq >= 3, about 8 GB of values per part and at least 3 parts, else 1.
+                               n_eq >= 3, about 16 GB of values per part and at least 3 parts, else 1.
                                Default 0 */
   int32_t contraction;      /* fea_contraction: how the FP32 Hex27 element matrices (full operator, up to
                                12 equations) are contracted; other element types and the residual use

@@ -1338,11 +1338,14 @@ fea_status fea_assemble_host(fea_mesh* m, const fea_pattern* cp, const void* vel
     }
   };
   // Large outputs: the equations are assembled in parts, each an independent assembly of its
-  // slices, so that part k's values travel back while part k+1 computes; about 8 GB of values
-  // per part (3 parts at least: 3 measured best of 3 and 6 on 5 GB of values).
+  // slices, so that part k's values travel back while part k+1 computes.  About 16 GB of values
+  // per part, 3 parts at least: fewer equations per part share each element's geometry less
+  // (Hex8 256^3: 44, 55, 87 and 173 ms for 4, 8, 16 and 32 equations), more parts overlap more
+  // of the copies; on 58 GB of values 4 parts took 389 ms, 2, 8 and 16 parts 424, 415 and
+  // 667 ms, and on 5 GB 3 parts measured best of 3 and 6.
   const int parts = o.host_parts > 0 ? std::min(o.host_parts, n_eq)
                     : (b_val > ((size_t)256 << 20) && n_eq >= 3)
-                        ? std::min<int>(n_eq, std::max<int>(3, (int)((b_val + (8ull << 30) - 1) / (8ull << 30))))
+                        ? std::min<int>(n_eq, std::max<int>(3, (int)((b_val + (16ull << 30) - 1) / (16ull << 30))))
                         : 1;
   const int per = (n_eq + parts - 1) / parts;
   if (o.accumulate) {  // the outputs travel in as well: every input first, then the parts
