@@ -477,26 +477,49 @@ fea_status plan_prepare(fea_rowowned_plan* P, int n_eq, int batch, bool* ok) {
 namespace ro {
 // Node-major copy of the per-step inputs, so that the (element, equation) threads of one
 // element read contiguous memory: out[n][f n_eq + q] for f = k, s, phi_old, then
-// out[n][3 n_eq + c] = u_c.  One block transposes 32 nodes through shared memory.
+// out[n][3 n_eq + c] = u_c.  One block transposes tn nodes (a multiple of 32) through shared
+// memory: a warp reads 4 tn bytes of one input row, then the block writes the tn records
+// contiguously.
 __global__ void k_fields_nodemajor(const float* __restrict__ kd, const float* __restrict__ sr,
                                    const float* __restrict__ phi, const float* __restrict__ vel, int64_t N, int n_eq,
-                                   float* __restrict__ out) {
-  extern __shared__ float tile[];  // [rec][33]
+                                   int tn, float* __restrict__ out) {
+  extern __shared__ float tile[];  // [rec][tn + 1]
   const int rec = 3 * n_eq + 3, lane = threadIdx.x & 31;
-  const int64_t n0 = (int64_t)blockIdx.x * 32, n = n0 + lane;
+  const int64_t n0 = (int64_t)blockIdx.x * tn;
   for (int j = threadIdx.x >> 5; j < rec; j += blockDim.x >> 5) {
     const float* src = j < n_eq       ? kd + (int64_t)j * N
                        : j < 2 * n_eq ? sr + (int64_t)(j - n_eq) * N
                        : j < 3 * n_eq ? phi + (int64_t)(j - 2 * n_eq) * N
                                       : vel + (int64_t)(j - 3 * n_eq) * N;
-    tile[j * 33 + lane] = n < N ? src[n] : 0.f;
+    for (int k = lane; k < tn; k += 32) {
+      const int64_t n = n0 + k;
+      tile[j * (tn + 1) + k] = n < N ? __ldcs(src + n) : 0.f;
+    }
   }
   __syncthreads();
-  const int cnt = (int)((N - n0) < 32 ? (N - n0) : 32);
+  const int cnt = (int)((N - n0) < tn ? (N - n0) : tn);
+  float* const o = out + n0 * rec;
   for (int idx = threadIdx.x; idx < cnt * rec; idx += blockDim.x) {
     const int node = idx / rec, j = idx - node * rec;
-    out[(n0 + node) * rec + j] = tile[j * 33 + node];
+    o[idx] = tile[j * (tn + 1) + node];
   }
+}
+
+// Launches k_fields_nodemajor for equations eq0 .. eq0 + eq_count - 1 of a into out: 128 nodes
+// per block, fewer where the [rec][tn + 1] tile would not fit in shared memory.
+fea_status fields_nodemajor(const AsmArgs<float>& a, float* out, cudaStream_t s) {
+  const int rec = 3 * a.eq_count + 3;
+  int tn = 128;
+  while (tn > 32 && sizeof(float) * (size_t)rec * (tn + 1) > 200 * 1024) tn /= 2;
+  const size_t tsm = sizeof(float) * (size_t)rec * (tn + 1);
+  if (tsm > (size_t)SMEM_LIMIT) return fail(FEA_ERR_ARG, "too many equations for the node-major field copy");
+  const int64_t fo = (int64_t)a.eq0 * a.n_node;
+  FEA_CUDA_TRY(cudaFuncSetAttribute(k_fields_nodemajor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
+  k_fields_nodemajor<<<(unsigned)((a.n_node + tn - 1) / tn), 256, tsm, s>>>(a.kd + fo, a.sr + fo, a.phi + fo, a.vel,
+                                                                            a.n_node, a.eq_count, tn, out);
+  FEA_CUDA_TRY(cudaGetLastError());
+  count_launches(1);
+  return FEA_OK;
 }
 }  // namespace ro
 
@@ -518,15 +541,7 @@ void plan_trim(fea_rowowned_plan* P, const std::vector<int>& keep) {
 // One group of equations [a.eq0, a.eq0 + a.eq_count) with the schedule of variant v.
 static fea_status assemble_group(ro::Variant* v, const AsmArgs<float>& a, int accumulate, cudaStream_t s) {
   const int rec = 3 * a.eq_count + 3;
-  const int64_t fo = (int64_t)a.eq0 * a.n_node;
-  {
-    const size_t tsm = sizeof(float) * rec * 33;
-    FEA_CUDA_TRY(cudaFuncSetAttribute(ro::k_fields_nodemajor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    ro::k_fields_nodemajor<<<(unsigned)((a.n_node + 31) / 32), 256, tsm, s>>>(a.kd + fo, a.sr + fo, a.phi + fo, a.vel,
-                                                                              a.n_node, a.eq_count, v->fnode);
-    FEA_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
-  }
+  FEA_TRY(ro::fields_nodemajor(a, v->fnode, s));
   ro::RoArgs r;
   r.a = a;
   r.fnode = v->fnode;
@@ -573,15 +588,7 @@ fea_status hex8_elem(float*& fnode, size_t& fnode_bytes, const AsmArgs<float>& a
     }
     fnode_bytes = need;
   }
-  const int64_t fo = (int64_t)a.eq0 * a.n_node;
-  {
-    const size_t tsm = sizeof(float) * rec * 33;
-    FEA_CUDA_TRY(cudaFuncSetAttribute(ro::k_fields_nodemajor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsm));
-    ro::k_fields_nodemajor<<<(unsigned)((a.n_node + 31) / 32), 256, tsm, s>>>(a.kd + fo, a.sr + fo, a.phi + fo, a.vel,
-                                                                              a.n_node, a.eq_count, fnode);
-    FEA_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
-  }
+  FEA_TRY(ro::fields_nodemajor(a, fnode, s));
   ro::RoArgs r{};
   r.a = a;
   r.fnode = fnode;
